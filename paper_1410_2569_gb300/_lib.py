@@ -1,0 +1,104 @@
+"""ctypes declarations of liblbm.so (include/lbm.h).  Marshalling only."""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+FSI = {"density": 0, "psi": 1, "modified": 2}
+WALL = {"neq": 0, "bb": 1}
+GHOST = {"copy": 0, "mirror": 1, "zero": 2}
+OMEGA = {"w": 0, "cs2w": 1}
+PREC = {"fp64": 0, "fp32": 1, "fp32_f64": 2}
+STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
+          4: "LBM_ERR_NONFINITE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
+
+# every symbol include/lbm.h declares
+EXPORTS = ["lbm_default_params", "lbm_create", "lbm_create_batch", "lbm_destroy",
+           "lbm_instance_size", "lbm_init_droplet", "lbm_set_density", "lbm_step", "lbm_sync",
+           "lbm_time", "lbm_get_fields", "lbm_get_populations", "lbm_diagnostics",
+           "lbm_set_gw_field", "lbm_set_launch", "lbm_selftest_wait_timeout", "lbm_last_error"]
+
+
+class LbmParams(ctypes.Structure):
+    _fields_ = [("eos", ctypes.c_int), ("eos_p", ctypes.c_double * 6),
+                ("G", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("tau_rho", ctypes.c_double), ("tau_e", ctypes.c_double),
+                ("tau_zeta", ctypes.c_double), ("tau_j", ctypes.c_double),
+                ("tau_q", ctypes.c_double),
+                ("tau_nu_L", ctypes.c_double), ("tau_nu_V", ctypes.c_double),
+                ("rho_L", ctypes.c_double), ("rho_V", ctypes.c_double),
+                ("wall", ctypes.c_int), ("ghost", ctypes.c_int), ("omega", ctypes.c_int),
+                ("prec", ctypes.c_int), ("rho_ref", ctypes.c_double)]
+
+
+class LbmInstanceDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("params", ctypes.POINTER(LbmParams)), ("solid", ctypes.c_void_p),
+                ("fsi", ctypes.c_int), ("gw_field", ctypes.c_void_p),
+                ("gw_uniform", ctypes.c_double)]
+
+
+class LbmDiag(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_long), ("mass", ctypes.c_double),
+                ("rho_max", ctypes.c_double), ("rho_min", ctypes.c_double),
+                ("u_max", ctypes.c_double), ("theta_deg", ctypes.c_double),
+                ("fit_rms", ctypes.c_double), ("xc", ctypes.c_double), ("yc", ctypes.c_double),
+                ("radius", ctypes.c_double), ("n_contour", ctypes.c_int),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load liblbm.so.  There is no fallback: a missing library is an error."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"liblbm.so not found at {path}; build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(path)
+    vp, i, d, l = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
+    P = ctypes.POINTER
+    sig = {
+        "lbm_default_params": (i, [P(LbmParams)]),
+        "lbm_create": (i, [i, i, P(LbmParams), vp, i, vp, d, vp, P(vp)]),
+        "lbm_create_batch": (i, [i, P(LbmInstanceDesc), vp, P(vp)]),
+        "lbm_destroy": (None, [vp]),
+        "lbm_instance_size": (i, [vp, i, P(i), P(i)]),
+        "lbm_init_droplet": (i, [vp, i, d, d, d, d]),
+        "lbm_set_density": (i, [vp, i, vp, i]),
+        "lbm_step": (i, [vp, l]),
+        "lbm_sync": (i, [vp]),
+        "lbm_time": (l, [vp]),
+        "lbm_get_fields": (i, [vp, i, vp, vp, vp, i]),
+        "lbm_get_populations": (i, [vp, i, vp, i]),
+        "lbm_diagnostics": (i, [vp, i, d, d, d, P(LbmDiag)]),
+        "lbm_set_gw_field": (i, [vp, i, vp]),
+        "lbm_set_launch": (i, [vp, i, i, i, i]),
+        "lbm_selftest_wait_timeout": (i, [vp, d]),
+        "lbm_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def check(status):
+    if status != 0:
+        raise LbmError(status, load().lbm_last_error().decode())
+    return status

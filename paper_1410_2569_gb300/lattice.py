@@ -1,0 +1,169 @@
+"""Python face of liblbm: the same calls as include/lbm.h, argument
+marshalling only.  Every step of the method runs in the library's CUDA
+kernels; PyTorch supplies the CUDA stream and, optionally, device output
+buffers."""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import FSI, GHOST, OMEGA, PREC, WALL, LbmDiag, LbmInstanceDesc, LbmParams, check
+
+_PARAM_KEYS = ("G", "sigma", "tau_rho", "tau_e", "tau_zeta", "tau_j", "tau_q", "tau_nu_L",
+               "tau_nu_V", "rho_L", "rho_V", "rho_ref")
+
+
+def default_params(**over):
+    """Parameters of Sec. III as a dict (lbm_default_params), with overrides.
+    EOS keys: kV, kM, kL (theta_V, theta_M, theta_L over cs^2), rho_1, rho_2."""
+    p = LbmParams()
+    check(_lib.load().lbm_default_params(ctypes.byref(p)))
+    d = {k: getattr(p, k) for k in _PARAM_KEYS}
+    d.update(kV=p.eos_p[0], kM=p.eos_p[1], kL=p.eos_p[2], rho_1=p.eos_p[3], rho_2=p.eos_p[4],
+             wall="neq", ghost="copy", omega="w", prec="fp64")
+    d.update(over)
+    return d
+
+
+def to_struct(d):
+    p = LbmParams()
+    check(_lib.load().lbm_default_params(ctypes.byref(p)))
+    for k in _PARAM_KEYS:
+        if k in d:
+            setattr(p, k, float(d[k]))
+    for j, k in enumerate(("kV", "kM", "kL", "rho_1", "rho_2")):
+        if k in d:
+            p.eos_p[j] = float(d[k])
+
+    def enum(v, table):
+        return table[v] if isinstance(v, str) else int(v)
+    p.wall = enum(d.get("wall", "neq"), WALL)
+    p.ghost = enum(d.get("ghost", "copy"), GHOST)
+    p.omega = enum(d.get("omega", "w"), OMEGA)
+    p.prec = enum(d.get("prec", "fp64"), PREC)
+    return p
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Lattice:
+    """One context: a single lattice (lbm_create) or a batch (lbm_create_batch).
+
+    instances: list of dicts with keys nx, ny, params, solid, fsi, gw."""
+
+    def __init__(self, instances, stream=None):
+        L = _lib.load()
+        self._L = L
+        self._keep = []
+        n = len(instances)
+        descs = (LbmInstanceDesc * n)()
+        self.shapes = []
+        for k, inst in enumerate(instances):
+            nx, ny = int(inst["nx"]), int(inst["ny"])
+            ps = to_struct(inst.get("params") or default_params())
+            self._keep.append(ps)
+            solid = inst.get("solid")
+            if solid is not None:
+                solid = np.ascontiguousarray(solid, dtype=np.uint8).reshape(ny, nx)
+                self._keep.append(solid)
+            gw = inst.get("gw", 0.0)
+            gw_field = None
+            if np.ndim(gw) != 0:
+                gw_field = np.ascontiguousarray(gw, dtype=np.float64).reshape(ny, nx)
+                self._keep.append(gw_field)
+            fsi = inst.get("fsi", "modified")
+            descs[k].nx, descs[k].ny = nx, ny
+            descs[k].params = ctypes.pointer(ps)
+            descs[k].solid = None if solid is None else solid.ctypes.data
+            descs[k].fsi = FSI[fsi] if isinstance(fsi, str) else int(fsi)
+            descs[k].gw_field = None if gw_field is None else gw_field.ctypes.data
+            descs[k].gw_uniform = 0.0 if gw_field is not None else float(gw)
+            self.shapes.append((ny, nx))
+        h = ctypes.c_void_p()
+        check(L.lbm_create_batch(n, descs, _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+        self._keep = []
+
+    @classmethod
+    def single(cls, nx, ny, params=None, solid=None, fsi="modified", gw=0.0, stream=None):
+        return cls([dict(nx=nx, ny=ny, params=params, solid=solid, fsi=fsi, gw=gw)], stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def t(self):
+        return self._L.lbm_time(self._h)
+
+    def init_droplet(self, x0, y0, R, width=2.0, inst=0):
+        check(self._L.lbm_init_droplet(self._h, inst, x0, y0, R, width))
+
+    def set_density(self, rho, inst=0):
+        if hasattr(rho, "data_ptr") and rho.is_cuda:
+            check(self._L.lbm_set_density(self._h, inst, ctypes.c_void_p(rho.data_ptr()), 1))
+        else:
+            r = np.ascontiguousarray(rho, dtype=np.float64)
+            check(self._L.lbm_set_density(self._h, inst, r.ctypes.data, 0))
+
+    def step(self, n=1):
+        check(self._L.lbm_step(self._h, int(n)))
+
+    def sync(self):
+        check(self._L.lbm_sync(self._h))
+
+    def set_launch(self, bx=0, h=0, persistent=False, graph=False):
+        check(self._L.lbm_set_launch(self._h, int(bx), int(h), int(persistent), int(graph)))
+
+    def fields(self, inst=0, device=False):
+        ny, nx = self.shapes[inst]
+        if device:
+            import torch
+            out = {k: torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+                   for k in ("rho", "ux", "uy")}
+            check(self._L.lbm_get_fields(self._h, inst, *[ctypes.c_void_p(out[k].data_ptr())
+                                                          for k in ("rho", "ux", "uy")], 1))
+            return out
+        out = {k: np.empty((ny, nx)) for k in ("rho", "ux", "uy")}
+        check(self._L.lbm_get_fields(self._h, inst, *[out[k].ctypes.data
+                                                      for k in ("rho", "ux", "uy")], 0))
+        return out
+
+    def populations(self, inst=0):
+        ny, nx = self.shapes[inst]
+        f = np.empty((9, ny, nx))
+        check(self._L.lbm_get_populations(self._h, inst, f.ctypes.data, 0))
+        return f
+
+    def diagnostics(self, inst=0, y_w=0.5, x_ref=None, d_min=3.0):
+        ny, nx = self.shapes[inst]
+        d = LbmDiag()
+        st = self._L.lbm_diagnostics(self._h, inst, float(y_w),
+                                     float(nx / 2 if x_ref is None else x_ref), float(d_min),
+                                     ctypes.byref(d))
+        out = d.as_dict()
+        out["status"] = st
+        return out
+
+    def set_gw_field(self, gw, inst=0):
+        g = np.ascontiguousarray(gw, dtype=np.float64)
+        check(self._L.lbm_set_gw_field(self._h, inst, g.ctypes.data))

@@ -1,0 +1,278 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: numbers
+the paper prints, closed forms, an independently written formulation (BGK
+with Guo forcing in velocity space), exact identities of the method, and
+conservation laws.  All run on the CPU in seconds.
+"""
+import numpy as np
+import pytest
+from scipy.optimize import brentq, fsolve
+
+import oracle
+from paper_1410_2569_gb300 import inputs
+
+CS2 = 1.0 / 3.0
+EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+@pytest.fixture(autouse=True)
+def _threads():
+    oracle.set_threads(4)
+
+
+# ---------------------------------------------------------------- Eq. (15)
+
+def _maxwell(p_of, rv0, rl0):
+    """Coexistence densities of an EOS p(rho) by the equal-area rule on the
+    specific volume: p(rv) = p(rl) = p0 and int_{1/rl}^{1/rv} (p - p0) dV = 0."""
+    from scipy.integrate import quad
+
+    def eqs(z):
+        rv, rl = z
+        p0 = p_of(rv)
+        # int (p(1/V) - p0) dV over V in [1/rl, 1/rv], with rho = 1/V
+        area = quad(lambda V: p_of(1.0 / V) - p0, 1.0 / rl, 1.0 / rv, limit=200,
+                    points=[1.0 / 481.04, 1.0 / 1.36])[0]
+        return [p_of(rl) - p0, area]
+    return fsolve(eqs, [rv0, rl0], xtol=1e-13)
+
+
+def test_spinodal_points_printed_in_sec3_follow_from_maxwell():
+    """Sec. III: rho_L = 500, rho_V = 1 correspond to rho_1 = 1.36 and
+    rho_2 = 481.04.  Solve the mechanical + chemical equilibrium conditions for
+    (rho_1, rho_2) with the oracle's Eq. (15) and round as the paper does."""
+    base = oracle.paper_params()
+
+    def residual(z):
+        r1, r2 = z
+        p = dict(base, rho_1=r1, rho_2=r2)
+        p_of = lambda r: oracle.p_eos(p, r)  # noqa: E731
+        p0 = p_of(1.0)
+        from scipy.integrate import quad
+        area = quad(lambda V: p_of(1.0 / V) - p0, 1.0 / 500.0, 1.0, limit=400,
+                    points=[1.0 / r2, 1.0 / r1])[0]
+        return [p_of(500.0) - p0, area]
+    r1, r2 = fsolve(residual, [1.3, 480.0], xtol=1e-13)
+    assert round(r1, 2) == 1.36 and round(r2, 2) == 481.04, (r1, r2)
+
+
+def test_printed_eos_coexistence():
+    """The printed (rounded) rho_1, rho_2 give coexistence densities within
+    0.2 % of the target rho_V = 1, rho_L = 500 (Sec. III)."""
+    p = oracle.paper_params()
+    rv, rl = _maxwell(lambda r: oracle.p_eos(p, r), 1.0, 500.0)
+    assert abs(rv - 1.0) < 2e-3 and abs(rl - 500.0) / 500 < 2e-3, (rv, rl)
+
+
+def test_eos_branches_and_psi_closed_form():
+    """p continuous at rho_1 and rho_2; psi = sqrt(2 (rho cs^2 - p)) for
+    G = -1 in closed form on each branch: 0.72 cs^2 rho (vapour),
+    2 cs^2 (1.04 rho - 0.68 rho_1) (middle), constant on the liquid branch."""
+    p = oracle.paper_params()
+    for r in (1.36, 481.04):
+        lo, hi = oracle.p_eos(p, r * (1 - 1e-13)), oracle.p_eos(p, r * (1 + 1e-13))
+        assert abs(lo - hi) < 1e-9
+    assert np.isclose(oracle.psi(p, 1.0), np.sqrt(0.72 * CS2), rtol=1e-15)
+    assert np.isclose(oracle.psi(p, 250.5), np.sqrt(2 * CS2 * (1.04 * 250.5 - 0.68 * 1.36)),
+                      rtol=1e-14)
+    liq = np.sqrt(2 * CS2 * (1.04 * 481.04 - 0.68 * 1.36))
+    for r in (481.5, 500.0, 545.0):
+        assert np.isclose(oracle.psi(p, r), liq, rtol=1e-14)
+
+
+# ---------------------------------------------------------------- MRT
+
+def test_transformation_matrix_orthogonal():
+    M, Minv = oracle.mrt_matrices()
+    assert np.array_equal(M @ M.T, np.diag([9.0, 36, 36, 6, 12, 6, 12, 4, 4]))
+    assert np.abs(Minv @ M - np.eye(9)).max() < 1e-15
+
+
+def test_moments_of_equilibrium_are_eq3():
+    """M f_eq(rho, v) equals Eq. (3) for the second-order D2Q9 equilibrium."""
+    M, _ = oracle.mrt_matrices()
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        rho = rng.uniform(0.5, 500)
+        vx, vy = rng.uniform(-0.1, 0.1, 2)
+        ev = EX * vx + EY * vy
+        feq = W * rho * (1 + 3 * ev + 4.5 * ev ** 2 - 1.5 * (vx * vx + vy * vy))
+        v2 = vx * vx + vy * vy
+        meq = rho * np.array([1, -2 + 3 * v2, 1 - 3 * v2, vx, -vx, vy, -vy, vx * vx - vy * vy,
+                              vx * vy])
+        assert np.allclose(M @ feq, meq, rtol=1e-13, atol=1e-12 * rho)
+
+
+def _bgk_guo_step(f, Fx, Fy, tau):
+    """Velocity-space BGK with Guo's forcing, then periodic streaming; an
+    independent formulation that MRT with equal rates and sigma = 0 must
+    reproduce exactly (S of Eq. (9) with sigma = 0 is M applied to Guo's
+    forcing term)."""
+    rho = f.sum(0)
+    jx = np.tensordot(EX, f, 1) + 0.5 * Fx
+    jy = np.tensordot(EY, f, 1) + 0.5 * Fy
+    vx, vy = jx / rho, jy / rho
+    out = np.empty_like(f)
+    for a in range(9):
+        ev = EX[a] * vx + EY[a] * vy
+        feq = W[a] * rho * (1 + 3 * ev + 4.5 * ev ** 2 - 1.5 * (vx ** 2 + vy ** 2))
+        Fa = W[a] * (1 - 0.5 / tau) * ((3 * (EX[a] - vx) + 9 * ev * EX[a]) * Fx +
+                                       (3 * (EY[a] - vy) + 9 * ev * EY[a]) * Fy)
+        post = f[a] - (f[a] - feq) / tau + Fa
+        out[a] = np.roll(np.roll(post, EY[a], axis=0), EX[a], axis=1)
+    return out
+
+
+@pytest.mark.parametrize("fsi", ["density", "modified"])
+def test_equal_rates_reduce_to_bgk_guo(fsi):
+    nx, ny, tau = 24, 20, 0.83
+    p = oracle.paper_params(sigma=0.0, tau_rho=tau, tau_e=tau, tau_zeta=tau, tau_j=tau,
+                            tau_q=tau, tau_nu_L=tau, tau_nu_V=tau)
+    o = oracle.Lattice(nx, ny, p, np.zeros((ny, nx), np.uint8), fsi, 0.0)
+    rng = np.random.default_rng(0)
+    rho0 = 200 + 150 * np.sin(2 * np.pi * np.arange(nx) / nx)[None, :] * \
+        np.cos(2 * np.pi * np.arange(ny) / ny)[:, None]
+    f0 = W[:, None, None] * rho0[None] * (1 + 0.05 * rng.standard_normal((9, ny, nx)))
+    o.set_populations(f0)
+    fl = o.fields()
+    o.step(1)
+    ref = _bgk_guo_step(f0, fl["Fx"], fl["Fy"], tau)
+    got = o.populations()
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-13
+
+
+# ---------------------------------------------------------------- forces
+
+def test_fluid_fluid_force_1d_reduces_to_central_difference():
+    """For psi varying along x only, sum_a w_a psi(x+e_a) e_a of Eq. (7) with
+    w = 1/3, 1/12 is the central difference (psi(x+1) - psi(x-1))/2 and has no
+    y component; likewise along y."""
+    nx, ny = 32, 6
+    p = oracle.paper_params()
+    x = np.arange(nx)
+    rho1d = 1.0 + 0.2 * np.sin(2 * np.pi * x / nx) + 100 * (np.abs(x - 16) < 5)
+    for axis in (1, 0):
+        rho = np.tile(rho1d, (ny, 1)) if axis == 1 else np.tile(rho1d[:, None], (1, ny))
+        shp = rho.shape
+        o = oracle.Lattice(shp[1], shp[0], p, np.zeros(shp, np.uint8), "density", 0.0)
+        o.set_density(rho)
+        fl = o.fields()
+        psi = np.vectorize(lambda r: oracle.psi(p, r))(rho)
+        cd = (np.roll(psi, -1, axis=axis) - np.roll(psi, 1, axis=axis)) / 2
+        F_along = fl["Fx"] if axis == 1 else fl["Fy"]
+        F_across = fl["Fy"] if axis == 1 else fl["Fx"]
+        assert np.allclose(F_along, -p["G"] * psi * cd, rtol=1e-13, atol=1e-13)
+        assert np.abs(F_across).max() < 1e-13
+
+
+@pytest.mark.parametrize("fsi", ["density", "psi", "modified"])
+@pytest.mark.parametrize("omega,factor", [("w", 0.5), ("cs2w", 1.0 / 6.0)])
+def test_fluid_solid_force_at_flat_wall(fsi, omega, factor):
+    """At a node whose row below is solid, sum_a omega_a s(x+e_a) e_a is
+    (0, -(omega_1 + 2 omega_diag)): -1/2 with omega = w (1/3, 1/12) and
+    -1/6 with omega = cs^2 w.  Hence F_ads = (0, factor G_w X) with
+    X = rho (Eq. 10), psi (Eq. 11), psi^2 (Eq. 14)."""
+    nx, ny, gw = 16, 12, 0.37
+    solid = inputs.flat_walls(nx, ny)
+    p = oracle.paper_params(omega=omega)
+    rho = np.full((ny, nx), 3.0)
+    rho[5:9, :] = 300.0
+    rho[1, :] = 2.0 + 0.1 * np.arange(nx)
+    out = {}
+    for g in (0.0, gw):
+        o = oracle.Lattice(nx, ny, p, solid, fsi, g)
+        o.set_density(rho)
+        out[g] = o.fields()
+    dFx = out[gw]["Fx"] - out[0.0]["Fx"]
+    dFy = out[gw]["Fy"] - out[0.0]["Fy"]
+    psi = out[0.0]["psi"]
+    X = {"density": rho, "psi": psi, "modified": psi * psi}[fsi]
+    assert np.allclose(dFy[1], factor * gw * X[1], rtol=1e-13)
+    assert np.abs(dFx[1]).max() < 1e-13
+    # the neutral top wall (G_w = 0 on row ny-1 here too: uniform G_w) pulls down
+    assert np.allclose(dFy[ny - 2], -factor * gw * X[ny - 2], rtol=1e-13)
+    assert np.abs(dFy[2:ny - 2]).max() == 0.0
+
+
+def test_wall_rule_gives_zero_momentum():
+    """After the wall rule of Sec. III.A, sum_a e_a f_a + F/2 = 0 at every wall
+    node, with F the force of that node's collision."""
+    nx, ny = 40, 30
+    solid = inputs.flat_walls(nx, ny)
+    o = oracle.Lattice(nx, ny, oracle.paper_params(), solid, "modified", 0.2)
+    o.init_droplet(20, 0.5, 10, 2.0)
+    o.step(30)
+    F = o.fields()
+    o.step(1)
+    f = o.populations()
+    for row in (1, ny - 2):
+        mx = np.tensordot(EX, f[:, row], 1) + 0.5 * F["Fx"][row]
+        my = np.tensordot(EY, f[:, row], 1) + 0.5 * F["Fy"][row]
+        scale = np.abs(f[:, row]).max()
+        assert np.abs(mx).max() < 1e-13 * scale and np.abs(my).max() < 1e-13 * scale
+
+
+# ---------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("case", ["periodic", "bb_flat", "bb_pillars"])
+def test_mass_conservation(case):
+    nx, ny = 48, 40
+    if case == "periodic":
+        solid, over = np.zeros((ny, nx), np.uint8), {}
+    elif case == "bb_flat":
+        solid, over = inputs.flat_walls(nx, ny), dict(wall="bb")
+    else:
+        solid, over = inputs.pillars(nx, ny, height=6, width=4, gap=3), dict(wall="bb",
+                                                                            ghost="zero")
+    o = oracle.Lattice(nx, ny, oracle.paper_params(**over), solid, "psi", 0.8)
+    o.init_droplet(24, 12, 9, 2.0)
+    m0 = o.fields()["rho"][solid == 0].sum()
+    o.step(1000)
+    m1 = o.fields()["rho"][solid == 0].sum()
+    assert abs(m1 - m0) / m0 < 1e-12, (m0, m1)
+
+
+@pytest.mark.parametrize("rho0", [0.9, 100.0, 490.0])
+def test_uniform_fluid_is_a_fixed_point(rho0):
+    nx, ny = 10, 8
+    o = oracle.Lattice(nx, ny, oracle.paper_params(), np.zeros((ny, nx), np.uint8), "psi", 1.0)
+    o.set_density(np.full((ny, nx), rho0))
+    o.step(20)
+    fl = o.fields()
+    assert np.abs(fl["rho"] - rho0).max() < 1e-12 * rho0
+    assert np.abs(fl["ux"]).max() < 1e-14 and np.abs(fl["uy"]).max() < 1e-14
+
+
+def test_mirror_symmetry_of_centred_droplet():
+    nx, ny = 64, 40
+    solid = inputs.flat_walls(nx, ny)
+    o = oracle.Lattice(nx, ny, oracle.paper_params(), solid, "density", 0.1)
+    o.init_droplet(0.0, 0.5, 14, 2.0)  # centred on x = 0: mirror x -> -x
+    o.step(500)
+    fl = o.fields()
+    mirror = np.roll(fl["rho"][:, ::-1], 1, axis=1)
+    assert np.abs(fl["rho"] - mirror).max() < 1e-9 * fl["rho"].max()
+    umir = -np.roll(fl["ux"][:, ::-1], 1, axis=1)
+    assert np.abs(fl["ux"] - umir).max() < 1e-9
+
+
+# ---------------------------------------------------------------- contact angle fit
+
+@pytest.mark.parametrize("theta", [30.0, 75.0, 90.0, 120.0, 160.0])
+def test_circle_fit_recovers_cap_angle(theta):
+    """A density field whose level set is an exact circular cap of known
+    angle: the fit returns that angle (closed form y_c = -R cos(theta))."""
+    nx, ny, R, y_w, xc = 200, 120, 40.0, 0.5, 100.0
+    yc = y_w - R * np.cos(np.radians(theta))
+    X, Y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    dist = np.sqrt((X - xc) ** 2 + (Y - yc) ** 2)
+    rho = 250.5 - (dist - R) * 10.0  # linear in distance: interpolation is exact on edges
+    solid = inputs.flat_walls(nx, ny)
+    d = oracle.contact_angle(rho, solid, 250.5, y_w, xc, d_min=3.0)
+    # linear interpolation of a linear-in-distance field is exact only along
+    # radial edges; the fit error is second order in 1/R
+    assert abs(d["theta_deg"] - theta) < 0.05, d
+    assert abs(d["radius"] - R) < 0.05
