@@ -1,0 +1,349 @@
+"""Throughput of the pseudopotential-LBM wetting step on GB300.
+
+Workload: the paper-shaped sweep -- 72 sessile droplets on 400 x 200
+lattices (radius 50 on a flat wall; density-based, pseudopotential-based and
+modified interactions at 12 G_w values each over the ranges of Sec. III.C;
+vapour/liquid viscosity ratios 1 and 10) held as one batched context.  One
+bench step = one time step of all 72 lattices (5.76 M nodes).  `value` is the
+FP32 shifted-population path (MLUPS, all nodes counted); the FP64 path is
+reported under "fp64".  Inputs are larger than L2 (415 MB FP32, 830 MB FP64
+of populations), so no L2 flush is needed between steps.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY, R = 400, 200, 50.0
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP64 pipe throughput of this GPU model, measured with a DFMA/DADD probe
+# (504 G FP64 instructions/s; 1.008 TFLOP/s counting an FMA as 2 flops)
+FP64_OPS_PER_S = 504e9
+BYTES_PER_NODE = {"fp32": 72.0, "fp32_f64": 72.0, "fp64": 144.0}
+
+
+def sweep_instances(prec):
+    from paper_1410_2569_gb300 import default_params, inputs
+    solid = inputs.flat_walls(NX, NY)
+    out = []
+    for c in inputs.sweep_cases():
+        p = default_params(prec=prec, tau_nu_L=c["tau_nu_L"], tau_nu_V=c["tau_nu_V"])
+        out.append(dict(nx=NX, ny=NY, params=p, solid=solid, fsi=c["fsi"], gw=c["gw"]))
+    return out
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def droplet_density(nx, ny, x0, y0, R, W, rho_L=500.0, rho_V=1.0):
+    """Host input of the end-to-end leg: a sessile-droplet density field with
+    a tanh interface of width W (minimum image in x)."""
+    x = np.arange(nx, dtype=np.float64)[None, :]
+    y = np.arange(ny, dtype=np.float64)[:, None]
+    dx = x - x0
+    dx -= nx * np.floor(dx / nx + 0.5)
+    r = np.sqrt(dx * dx + (y - y0) ** 2)
+    return rho_V + 0.5 * (rho_L - rho_V) * (1.0 - np.tanh(2.0 * (r - R) / W))
+
+
+def time_device(lat, stream, steps, warmup):
+    import torch
+    lat.step(warmup)
+    lat.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    lat.sync()
+    return e0.elapsed_time(e1) / 1000.0
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_1410_2569_gb300 as lbm
+    from paper_1410_2569_gb300 import inputs
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    nodes = len(inputs.sweep_cases()) * NX * NY
+    results = {}
+    y_w = inputs.wall_height("copy")
+    for prec in ("fp32", "fp64"):
+        insts = sweep_instances(prec)
+        lat = lbm.Lattice(insts, stream=stream)
+        for k in range(len(insts)):
+            lat.init_droplet(NX / 2, y_w, R, inputs.SWEEP_WIDTH, inst=k)
+        if args.launch:
+            bx, h, pers, graph = (int(v) for v in args.launch.split(","))
+            lat.set_launch(bx, h, pers, graph)
+        # warm-up, then the timed region bracketed by barrier + synchronize
+        lat.step(args.warmup)
+        lat.sync()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with Clocks(local) as clk:
+            dt = time_device(lat, stream, args.steps, 0)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t = torch.tensor([dt], device="cuda")
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+        mlups = ws * nodes * args.steps / dt / 1e6
+        # contact angle of one tracked instance after warm-up + timed steps
+        d = lat.diagnostics(inst=11, y_w=y_w, x_ref=NX / 2)
+        results[prec] = dict(dt=dt, mlups=mlups, clocks=clk.summary(), theta=d["theta_deg"],
+                             lat=lat)
+    # end-to-end through the C ABI with host buffers: host density fields in,
+    # `chunk` steps, host rho/ux/uy fields out, per e2e iteration
+    e2e = None
+    if rank == 0 or ws > 1:
+        lat = results["fp32"]["lat"]
+        n_inst = len(inputs.sweep_cases())
+        host_rho = torch.empty((NY, NX), dtype=torch.float64).pin_memory().numpy()
+        host_out = {k: torch.empty((NY, NX), dtype=torch.float64).pin_memory().numpy()
+                    for k in ("rho", "ux", "uy")}
+        host_rho[:] = droplet_density(NX, NY, NX / 2, y_w, R, inputs.SWEEP_WIDTH)
+        chunk, iters = max(1, args.steps // 2), 2
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            for k in range(n_inst):
+                lat.set_density(host_rho, inst=k)
+            lat.step(chunk)
+            for k in range(n_inst):
+                lat.fields(k, out=host_out)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": round(ws * nodes * chunk * iters / te / 1e6, 2), "unit": "MLUPS",
+               "h2d_bytes_per_step": n_inst * NX * NY * 8 / chunk,
+               "d2h_bytes_per_step": 3 * n_inst * NX * NY * 8 / chunk,
+               "steps_per_call": chunk}
+    for r in results.values():
+        r.pop("lat", None)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    hbm, peak_kind = measured_peaks()
+    f32, f64 = results["fp32"], results["fp64"]
+
+    def roof(prec, dt, steps):
+        achieved = nodes * BYTES_PER_NODE[prec] * steps / dt / 1e9  # per GPU
+        return achieved
+    ach32 = roof("fp32", f32["dt"], args.steps)
+    ach64 = roof("fp64", f64["dt"], args.steps)
+    # FP64 step: FP64 instructions per node counted from the source arithmetic
+    # (pull + density 8, psi ~12, collision ~120); FP64-pipe bound on this GPU
+    fp64_ops_node = 140.0
+    fp64_alu = nodes * fp64_ops_node * args.steps / f64["dt"] / 1e9
+    cpu = cpu_baseline(args) if not args.no_cpu else None
+    line = {
+        "metric": "D2Q9 MLUPS & % HBM roofline, FP32 vs FP64 at <=0.5 deg contact-angle error",
+        "value": round(f32["mlups"], 2),
+        "unit": "MLUPS",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(f32["dt"] / args.steps * 1e3, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "paper-shaped sweep: 72 sessile droplets, 400x200 each, "
+                               "3 interactions x 12 G_w x viscosity ratio {1,10}, R=50",
+                   "nodes_per_gpu": nodes, "lattice": [NX, NY], "instances": 72,
+                   "l2": "inputs larger than L2 (415 MB FP32 populations), no flush",
+                   "parallelism": f"independent sweeps per GPU x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": round(ach32, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(ach32 / hbm, 4), "traffic": None,
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_node": BYTES_PER_NODE["fp32"]},
+        "fp64": {"value": round(f64["mlups"], 2), "unit": "MLUPS",
+                 "ms_per_step": round(f64["dt"] / args.steps * 1e3, 4),
+                 "roofline": {"bound": "alu", "achieved": round(fp64_alu, 1),
+                              "peak": FP64_OPS_PER_S / 1e9, "unit": "G FP64 ops/s",
+                              "frac": round(fp64_alu * 1e9 / FP64_OPS_PER_S, 4),
+                              "fp64_ops_per_node": fp64_ops_node,
+                              "hbm_achieved_gbs": round(ach64, 1),
+                              "hbm_frac": round(ach64 / hbm, 4)},
+                 "clocks": f64["clocks"]},
+        "theta_fp32_vs_fp64_deg": round(abs(f32["theta"] - f64["theta"]), 6),
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": f32["clocks"],
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(args, budget_s=None):
+    """The FP64 oracle as it stands on this host's cores: a bounded sample of
+    the sweep (the first instances of the batch for a few steps)."""
+    import oracle
+    from paper_1410_2569_gb300 import inputs
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    budget = budget_s if budget_s is not None else args.cpu_seconds
+    solid = inputs.flat_walls(NX, NY)
+    cases = inputs.sweep_cases()
+    y_w = inputs.wall_height("copy")
+    done_nodes, t_used, n_inst, steps_each = 0, 0.0, 0, 0
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < budget and k < len(cases):
+        c = cases[k]
+        p = oracle.paper_params(tau_nu_L=c["tau_nu_L"], tau_nu_V=c["tau_nu_V"])
+        o = oracle.Lattice(NX, NY, p, solid, c["fsi"], c["gw"])
+        o.init_droplet(NX / 2, y_w, R, inputs.SWEEP_WIDTH)
+        ts = time.perf_counter()
+        steps = 0
+        while time.perf_counter() - t0 < budget and steps < 200:
+            o.step(10)
+            steps += 10
+        t_used += time.perf_counter() - ts
+        done_nodes += NX * NY * steps
+        n_inst += 1
+        steps_each = max(steps_each, steps)
+        k += 1
+    return {"value": round(done_nodes / t_used / 1e6, 3), "unit": "MLUPS", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{n_inst} of the 72 sweep lattices (400x200), up to {steps_each} steps "
+                      f"each, {t_used:.1f} s of CPU time"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    cpu = cpu_baseline(args, budget_s=max(5.0, args.cpu_seconds))
+    line = {
+        "metric": "D2Q9 MLUPS & % HBM roofline, FP32 vs FP64 at <=0.5 deg contact-angle error",
+        "value": cpu["value"], "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(72 * NX * NY / (cpu["value"] * 1e6) * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": "paper-shaped sweep: 72 sessile droplets, 400x200 each, "
+                               "3 interactions x 12 G_w x viscosity ratio {1,10}, R=50",
+                   "nodes_per_gpu": 72 * NX * NY, "lattice": [NX, NY], "instances": 72},
+        "cpu_baseline": cpu,
+        "e2e": {"value": cpu["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--launch", default="", help="bx,h,persistent,graph")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

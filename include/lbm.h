@@ -1,0 +1,227 @@
+/*
+ * liblbm: GB300 (sm_103a) library for the time step of the D2Q9
+ * multiple-relaxation-time pseudopotential (Shan-Chen) lattice Boltzmann
+ * model with fluid-solid interaction, after Li, Luo, Kang & Chen,
+ * "Contact angles in the pseudopotential lattice Boltzmann modeling of
+ * wetting" (Sec. II: Eqs. (1)-(11), (14); Sec. III: Eq. (15), wall rule,
+ * initial droplet Eq. (16)).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Lattice: nx * ny nodes, node (x, y) at index y * nx + x (x fastest),
+ * periodic in x and in y; solid nodes (switch function s = 1) form walls.
+ * Velocities e0=(0,0) e1=(1,0) e2=(0,1) e3=(-1,0) e4=(0,-1) e5=(1,1)
+ * e6=(-1,1) e7=(-1,-1) e8=(1,-1); populations f_alpha laid out [9][ny][nx]
+ * whenever they cross this interface.  Lattice units: c = delta_t = 1,
+ * cs^2 = 1/3.
+ *
+ * Pointers: every array argument is a plain pointer.  Inputs are host
+ * pointers unless the call takes a *_is_device flag; they are copied during
+ * the call and may be freed afterwards.  Outputs are caller-owned buffers of
+ * the stated length.  The context owns all device memory it allocates.
+ *
+ * Errors: every call returns an lbm_status; nothing aborts or throws across
+ * this boundary.  lbm_last_error() returns a message for the calling thread.
+ * Errors found on the device during lbm_step (non-finite density, a timed-out
+ * grid barrier) latch in the context and are returned by the next call that
+ * synchronises (lbm_diagnostics, lbm_get_fields, lbm_sync).
+ *
+ * Streams: a context enqueues all its work on the CUDA stream given at
+ * creation (NULL = the legacy default stream).  Calls on different contexts
+ * may come from different threads; calls on one context must not overlap.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = 1,       /* invalid argument or configuration */
+  LBM_ERR_OOM = 2,       /* device or host allocation failed */
+  LBM_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+  LBM_ERR_NONFINITE = 4, /* non-finite or non-positive density on a fluid node */
+  LBM_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
+  LBM_ERR_STATE = 6      /* call not valid in the context's current state */
+} lbm_status;
+
+/* Fluid-solid interaction F_ads: Eq. (10) density-based, Eq. (11)
+   pseudopotential-based, Eq. (14) the paper's modified pseudopotential-based
+   interaction with phi(x) = psi(x). */
+typedef enum { LBM_FSI_DENSITY = 0, LBM_FSI_PSI = 1, LBM_FSI_MODIFIED = 2 } lbm_fsi;
+
+/* Equation of state: the piecewise-linear EOS of Eq. (15). */
+typedef enum { LBM_EOS_PIECEWISE_LINEAR = 0 } lbm_eos;
+
+/* Wall treatment.  LBM_WALL_NEQ_ONNODE: the rule quoted in Sec. III.A for a
+   wall below the node (f2 = f4, f5 = f7 - (f1 - f3)/2 - (Fx + Fy)/4,
+   f6 = f8 + (f1 - f3)/2 + (Fx - Fy)/4, with F the node's force of the same
+   step), mirrored in y for a wall above; walls must be whole solid rows.
+   LBM_WALL_HALFWAY_BB: halfway bounce-back on every fluid-solid link, any
+   solid mask. */
+typedef enum { LBM_WALL_NEQ_ONNODE = 0, LBM_WALL_HALFWAY_BB = 1 } lbm_wall;
+
+/* How Eq. (7) treats solid neighbours.  Sec. III.A applies Eq. (7) at the
+   wall through a ghost layer: COPY gives a solid node the psi of the fluid
+   node next to it along the wall normal, MIRROR the psi of the fluid node
+   two rows away (both need whole solid rows).  ZERO gives solid nodes
+   psi = 0.  SKIP does not apply Eq. (7) at fluid nodes that have a solid
+   neighbour (Sec. III.B, rough surfaces); any mask. */
+typedef enum {
+  LBM_GHOST_COPY = 0,
+  LBM_GHOST_MIRROR = 1,
+  LBM_GHOST_ZERO = 2,
+  LBM_GHOST_SKIP = 3
+} lbm_ghost;
+
+/* Weights omega_alpha of Eqs. (10), (11), (14).  LBM_OMEGA_W: w_alpha of
+   Eq. (7), 1/3 and 1/12, under which the G_w values printed with Figs. 2-4
+   give the printed contact angles (default).  LBM_OMEGA_CS2W: cs^2 w_alpha,
+   1/9 and 1/36, the sentence after Eq. (10) read literally. */
+typedef enum { LBM_OMEGA_W = 0, LBM_OMEGA_CS2W = 1 } lbm_omega;
+
+/* Storage and arithmetic.  LBM_FP64: populations stored and collided in
+   FP64.  LBM_FP32_SHIFTED: populations stored and collided in FP32 as
+   f - w_alpha rho_ref; density summed with error-free FP32 transformations
+   (FP64-grade, no FP64 instructions on the step path); psi evaluated from
+   that density and rounded once.  LBM_FP32_SHIFTED_F64: as LBM_FP32_SHIFTED
+   but density summed and psi evaluated in IEEE FP64 instructions. */
+typedef enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1, LBM_FP32_SHIFTED_F64 = 2 } lbm_precision;
+
+typedef struct {
+  lbm_eos eos;
+  /* Eq. (15): theta_V, theta_M, theta_L in units of cs^2, then rho_1, rho_2 */
+  double eos_p[6];
+  double G;     /* interaction strength of Eq. (7); psi needs G < 0 */
+  double sigma; /* Eq. (9) */
+  /* relaxation times of Eq. (2) */
+  double tau_rho, tau_e, tau_zeta, tau_j, tau_q;
+  /* tau_nu in liquid and vapour (Sec. III.C); when they differ tau_nu varies
+     linearly in rho between rho_V and rho_L, clamped to the two values.
+     rho_L and rho_V also set the contact-angle level (rho_L + rho_V) / 2. */
+  double tau_nu_L, tau_nu_V, rho_L, rho_V;
+  lbm_wall wall;
+  lbm_ghost ghost;
+  lbm_omega omega;
+  lbm_precision prec;
+  double rho_ref; /* shift of the FP32 storage (ignored for LBM_FP64) */
+} lbm_params;
+
+/* One lattice of a batch (lbm_create_batch). */
+typedef struct {
+  int nx, ny;
+  const lbm_params* params; /* all instances of a batch share params->prec */
+  const uint8_t* solid;     /* [ny][nx], nonzero = solid; NULL = no solid */
+  lbm_fsi fsi;
+  const double* gw_field;   /* [ny][nx] G_w read on solid nodes; NULL = uniform */
+  double gw_uniform;
+} lbm_instance_desc;
+
+typedef struct {
+  long step;
+  double mass;      /* sum of rho over fluid nodes (FP64) */
+  double rho_max;   /* over fluid nodes (Sec. III.B, Table I) */
+  double rho_min;
+  double u_max;     /* max |v| over fluid nodes, v of Eq. (6) (Sec. III.C) */
+  double theta_deg; /* contact angle of the circle fitted to rho = (rho_L + rho_V)/2 */
+  double fit_rms;   /* rms distance of the contour points from the circle */
+  double xc, yc, radius;
+  int n_contour;    /* contour points used by the fit */
+  lbm_status status;
+} lbm_diag;
+
+/* Fills *p with the parameters of Sec. III: theta_V = 0.64 cs^2,
+   theta_M = -0.04 cs^2, theta_L = cs^2, rho_1 = 1.36, rho_2 = 481.04, G = -1,
+   sigma = 0.084, tau_rho = tau_j = 1, 1/tau_e = 1/tau_zeta = 0.8,
+   1/tau_q = 1.1, tau_nu = 1.1, rho_L = 500, rho_V = 1, NEQ wall, COPY ghost,
+   LBM_OMEGA_W, LBM_FP64, rho_ref = rho_V. */
+lbm_status lbm_default_params(lbm_params* p);
+
+/* Creates a context holding one lattice.  solid: [ny][nx] host array (NULL =
+   no solid); gw_field: [ny][nx] host array of G_w read on solid nodes (NULL =
+   gw_uniform on every solid node).  The populations start at zero: call
+   lbm_init_droplet or lbm_set_density before stepping.  stream: a
+   cudaStream_t or NULL.  LBM_ERR_ARG for nx < 3, ny < 4, tau <= 0.5, G >= 0,
+   a non-flat mask with the NEQ wall or a COPY/MIRROR ghost, or a fluid node
+   with solid directly above and below. */
+lbm_status lbm_create(int nx, int ny, const lbm_params* p, const uint8_t* solid, lbm_fsi fsi,
+                      const double* gw_field, double gw_uniform, void* stream, lbm_ctx** out);
+
+/* Creates a context holding count independent lattices of possibly different
+   sizes, parameters, interactions and G_w; lbm_step advances all of them in
+   one launch per time step (or one persistent launch, lbm_set_launch). */
+lbm_status lbm_create_batch(int count, const lbm_instance_desc* descs, void* stream,
+                            lbm_ctx** out);
+
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Number of instances and the size of instance inst. */
+lbm_status lbm_instance_size(const lbm_ctx* ctx, int inst, int* nx, int* ny);
+
+/* Initial droplet (Sec. III.A, Eq. (16) with a smooth interface):
+   rho = rho_V + (rho_L - rho_V)/2 * (1 - tanh(2 (r - R) / width)), r the
+   distance to (x0, y0) with the minimum image in x; f_alpha = w_alpha rho
+   (fluid at rest) on fluid nodes.  Resets the step counter. */
+lbm_status lbm_init_droplet(lbm_ctx* ctx, int inst, double x0, double y0, double R,
+                            double width);
+
+/* Fluid at rest with the density field rho [ny][nx] (host or device FP64). */
+lbm_status lbm_set_density(lbm_ctx* ctx, int inst, const double* rho, int src_is_device);
+
+/* Advances every instance by n time steps.  Asynchronous: returns after
+   enqueueing on the context's stream. */
+lbm_status lbm_step(lbm_ctx* ctx, long n);
+
+/* Waits for the context's stream; returns a latched device error if any. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+long lbm_time(const lbm_ctx* ctx);
+
+/* rho and v of Eq. (6) at the current time, FP64 [ny][nx] each (NULL skips
+   one).  Solid nodes read 0.  dst_is_device: the pointers are device memory.
+   Synchronises. */
+lbm_status lbm_get_fields(lbm_ctx* ctx, int inst, double* rho, double* ux, double* uy,
+                          int dst_is_device);
+
+/* Populations f_alpha(x, t) after streaming and the wall rule (the state
+   Eq. (6) is evaluated on), FP64 [9][ny][nx]; FP32 storage is shifted back.
+   Solid nodes read 0.  Synchronises. */
+lbm_status lbm_get_populations(lbm_ctx* ctx, int inst, double* f, int dst_is_device);
+
+/* Diagnostics of instance inst: mass, rho_max, rho_min, max |v|, and the
+   contact angle of the circle fitted (algebraic least squares) to the
+   points where rho crosses (rho_L + rho_V)/2 on edges between fluid nodes,
+   x unwrapped about x_ref, points closer than d_min to the wall height y_w
+   dropped; theta = 90 deg + asin((yc - y_w)/R).  Synchronises. */
+lbm_status lbm_diagnostics(lbm_ctx* ctx, int inst, double y_w, double x_ref, double d_min,
+                           lbm_diag* out);
+
+/* Replaces the G_w field of instance inst ([ny][nx] host, read on solid
+   nodes) and rebuilds the wall vectors of the fluid-solid force. */
+lbm_status lbm_set_gw_field(lbm_ctx* ctx, int inst, const double* gw);
+
+/* Launch shape of lbm_step: bx threads per block along x, h rows per block
+   (0 = choose automatically), persistent = 1 runs all n steps in one
+   cooperative launch with a bounded grid barrier between steps,
+   graph = 1 captures the n per-step launches in a CUDA graph. */
+lbm_status lbm_set_launch(lbm_ctx* ctx, int bx, int h, int persistent, int graph);
+
+/* Self-test of the bounded device-side wait used by the persistent step
+   kernel's grid barrier: one block waits for an arrival that never comes and
+   must give up after `seconds` (0 < seconds <= 10).  Returns LBM_ERR_TIMEOUT
+   when the wait gave up as designed; any other status means it did not. */
+lbm_status lbm_selftest_wait_timeout(void* stream, double seconds);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

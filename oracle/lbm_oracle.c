@@ -32,7 +32,9 @@
  *   - the wall rule uses F(x, t), the force of the same node's collision in
  *     the same step; the top wall uses the rule mirrored in y.
  *   - ghost psi: COPY takes psi of the fluid node next to the solid node
- *     along the wall normal, MIRROR the node two rows away, ZERO uses 0.
+ *     along the wall normal, MIRROR the node two rows away, ZERO uses 0;
+ *     SKIP does not apply Eq. (7) at fluid nodes touching solid (Sec. III.B:
+ *     rough surfaces without a ghost layer).
  *   - tau_nu varies linearly with rho between rho_V and rho_L (clamped)
  *     when the liquid and vapour values differ (Sec. III.C).
  *   - M is the orthogonal D2Q9 basis whose rows give the equilibria of
@@ -149,7 +151,9 @@ static int mask_rows_flat(int nx, int ny, const uint8_t* s) {
 oracle_lbm* oracle_create(int nx, int ny, const oracle_params* p, const uint8_t* solid, int fsi,
                           const double* gw_field, double gw_uniform) {
   if (nx < 1 || ny < 3 || !p || fsi < 0 || fsi > 2) return NULL;
-  if (p->wall == ORC_WALL_NEQ || p->ghost != ORC_GHOST_ZERO) {
+  const int flat = p->wall == ORC_WALL_NEQ || p->ghost == ORC_GHOST_COPY ||
+                   p->ghost == ORC_GHOST_MIRROR;
+  if (flat) {
     /* the wall rule of Sec. III.A and the ghost layer are defined for flat walls */
     if (solid && !mask_rows_flat(nx, ny, solid)) return NULL;
   }
@@ -170,7 +174,7 @@ oracle_lbm* oracle_create(int nx, int ny, const oracle_params* p, const uint8_t*
     o->s[i] = solid ? (solid[i] != 0) : 0;
     o->gw[i] = o->s[i] ? (gw_field ? gw_field[i] : gw_uniform) : 0.0;
   }
-  if (p->wall == ORC_WALL_NEQ || p->ghost != ORC_GHOST_ZERO) {
+  if (flat) {
     /* a fluid node may not have solid both directly above and below */
     for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x)
@@ -291,6 +295,12 @@ static void macroscopic(oracle_lbm* o) {
       }
       double Fmx = -p->G * o->psi[i] * sx;
       double Fmy = -p->G * o->psi[i] * sy;
+      if (p->ghost == ORC_GHOST_SKIP) {
+        /* Eq. (7) not applied next to the wall (Sec. III.B) */
+        int touches = 0;
+        for (int a = 1; a < Q; ++a) touches |= o->s[nid(o, x + ex[a], y + ey[a])];
+        if (touches) Fmx = Fmy = 0.0;
+      }
       double X;
       if (o->fsi == ORC_FSI_DENSITY) X = o->rho[i];                       /* Eq. (10) */
       else if (o->fsi == ORC_FSI_PSI) X = o->psi[i];                      /* Eq. (11) */

@@ -1,0 +1,722 @@
+// C ABI of liblbm: context management, validation, host-side set-up of the
+// per-node wall data, stepping and field read-back (declared in lbm.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_diag.cuh"
+#include "lbm_internal.cuh"
+
+using namespace lbm;
+
+static thread_local std::string g_err;
+
+static lbm_status fail(lbm_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,        \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+extern "C" const char* lbm_last_error(void) { return g_err.c_str(); }
+
+namespace {
+
+struct Inst {
+  int nx = 0, ny = 0;
+  lbm_params p{};
+  lbm_fsi fsi = LBM_FSI_MODIFIED;
+  std::vector<uint8_t> solid;
+  std::vector<double> gw;
+  std::vector<uint16_t> flags;
+  std::vector<uint8_t> row_plain;
+  // device
+  void* f[2] = {nullptr, nullptr};
+  void* Fw[2] = {nullptr, nullptr};
+  uint16_t* d_flags = nullptr;
+  uint8_t* d_row_plain = nullptr;
+  double2* d_A = nullptr;
+  InstDesc desc{};
+};
+
+}  // namespace
+
+struct lbm_ctx {
+  int prec = LBM_FP64;
+  cudaStream_t stream = nullptr;
+  std::vector<Inst> inst;
+  InstDesc* d_desc = nullptr;
+  WorkItem* d_items = nullptr;
+  int n_items = 0;
+  int* d_err = nullptr;       // [0] latched error bits
+  unsigned* d_barrier = nullptr;  // [0] arrival counter, [1] error word of the persistent kernel
+  int parity = 0;
+  long t = 0;
+  int bx = 0, h = 0, persistent = 0, use_graph = 0;
+  int bx_used = 0;
+  // CUDA graphs of n launches, keyed by (n, parity)
+  std::map<std::pair<long, int>, cudaGraphExec_t> graphs;
+  // scratch for field read-back and diagnostics
+  size_t scratch_n = 0;
+  double *d_rho = nullptr, *d_psi = nullptr, *d_ux = nullptr, *d_uy = nullptr;
+  DiagScratch diag{};
+};
+
+static size_t tsize(int prec) { return prec == LBM_FP64 ? sizeof(double) : sizeof(float); }
+
+extern "C" lbm_status lbm_default_params(lbm_params* p) {
+  if (!p) return fail(LBM_ERR_ARG, "lbm_default_params: NULL");
+  memset(p, 0, sizeof *p);
+  p->eos = LBM_EOS_PIECEWISE_LINEAR;
+  p->eos_p[0] = 0.64;
+  p->eos_p[1] = -0.04;
+  p->eos_p[2] = 1.0;
+  p->eos_p[3] = 1.36;
+  p->eos_p[4] = 481.04;
+  p->G = -1.0;
+  p->sigma = 0.084;
+  p->tau_rho = 1.0;
+  p->tau_e = 1.0 / 0.8;
+  p->tau_zeta = 1.0 / 0.8;
+  p->tau_j = 1.0;
+  p->tau_q = 1.0 / 1.1;
+  p->tau_nu_L = 1.1;
+  p->tau_nu_V = 1.1;
+  p->rho_L = 500.0;
+  p->rho_V = 1.0;
+  p->wall = LBM_WALL_NEQ_ONNODE;
+  p->ghost = LBM_GHOST_COPY;
+  p->omega = LBM_OMEGA_W;
+  p->prec = LBM_FP64;
+  p->rho_ref = 1.0;
+  return LBM_OK;
+}
+
+static lbm_status validate_params(const lbm_params* p) {
+  if (!p) return fail(LBM_ERR_ARG, "params is NULL");
+  if (p->eos != LBM_EOS_PIECEWISE_LINEAR) return fail(LBM_ERR_ARG, "unknown EOS %d", (int)p->eos);
+  if (!(p->G < 0.0)) return fail(LBM_ERR_ARG, "G must be negative for a real psi (got %g)", p->G);
+  if (!(p->eos_p[3] > 0.0 && p->eos_p[4] > p->eos_p[3]))
+    return fail(LBM_ERR_ARG, "need 0 < rho_1 < rho_2");
+  const double taus[] = {p->tau_rho, p->tau_e, p->tau_zeta, p->tau_j, p->tau_q, p->tau_nu_L,
+                         p->tau_nu_V};
+  for (double t : taus)
+    if (!(t > 0.5) || !isfinite(t)) return fail(LBM_ERR_ARG, "relaxation times must exceed 1/2");
+  if (!(p->sigma >= 0.0)) return fail(LBM_ERR_ARG, "sigma must be >= 0");
+  if (!(p->rho_L > p->rho_V && p->rho_V > 0.0)) return fail(LBM_ERR_ARG, "need rho_L > rho_V > 0");
+  if ((int)p->wall < 0 || (int)p->wall > 1) return fail(LBM_ERR_ARG, "unknown wall %d", (int)p->wall);
+  if ((int)p->ghost < 0 || (int)p->ghost > 3) return fail(LBM_ERR_ARG, "unknown ghost %d", (int)p->ghost);
+  if ((int)p->omega < 0 || (int)p->omega > 1) return fail(LBM_ERR_ARG, "unknown omega %d", (int)p->omega);
+  if ((int)p->prec < 0 || (int)p->prec > 2) return fail(LBM_ERR_ARG, "unknown precision %d", (int)p->prec);
+  if (!isfinite(p->rho_ref)) return fail(LBM_ERR_ARG, "rho_ref must be finite");
+  return LBM_OK;
+}
+
+static inline int wrap(int a, int n) { return ((a % n) + n) % n; }
+
+static const int EX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+// node flags and plain-row table from the solid mask
+static lbm_status build_flags(Inst& I) {
+  const int nx = I.nx, ny = I.ny;
+  const bool flat_needed = I.p.wall == LBM_WALL_NEQ_ONNODE || I.p.ghost == LBM_GHOST_COPY ||
+                           I.p.ghost == LBM_GHOST_MIRROR;
+  auto S = [&](int x, int y) { return I.solid[(size_t)wrap(y, ny) * nx + wrap(x, nx)] != 0; };
+  if (flat_needed) {
+    for (int y = 0; y < ny; ++y)
+      for (int x = 1; x < nx; ++x)
+        if (S(x, y) != S(0, y))
+          return fail(LBM_ERR_ARG,
+                      "row %d is partly solid: the NEQ wall rule and COPY/MIRROR ghosts need "
+                      "walls made of whole solid rows (use LBM_WALL_HALFWAY_BB + LBM_GHOST_ZERO)",
+                      y);
+  }
+  I.flags.assign((size_t)nx * ny, 0);
+  I.row_plain.assign(ny, 1);
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      uint16_t fl = 0;
+      if (S(x, y)) {
+        fl |= NF_SELF_SOLID;
+        if (!S(x, y + 1)) fl |= NF_GHOST_UP;
+        else if (!S(x, y - 1)) fl |= NF_GHOST_DOWN;
+        if (I.p.ghost == LBM_GHOST_MIRROR) {
+          if ((fl & NF_GHOST_UP) && S(x, y + 2))
+            return fail(LBM_ERR_ARG, "MIRROR ghost needs two fluid rows above solid row %d", y);
+          if ((fl & NF_GHOST_DOWN) && S(x, y - 2))
+            return fail(LBM_ERR_ARG, "MIRROR ghost needs two fluid rows below solid row %d", y);
+        }
+        if ((fl & NF_GHOST_UP) && flat_needed && I.p.ghost != LBM_GHOST_ZERO &&
+            I.p.ghost != LBM_GHOST_SKIP && !S(x, y - 1))
+          return fail(LBM_ERR_ARG, "solid row %d has fluid on both sides; COPY/MIRROR ghosts "
+                                   "need walls at least two rows thick", y);
+      } else {
+        for (int a = 1; a < Q; ++a)
+          if (S(x - EX[a], y - EY[a])) fl |= (uint16_t)(1u << a);
+        if (S(x, y - 1) && S(x, y + 1))
+          return fail(LBM_ERR_ARG, "fluid node (%d,%d) has solid directly above and below", x, y);
+        if (I.p.wall == LBM_WALL_NEQ_ONNODE) {
+          if (S(x, y - 1)) fl |= NF_NEQ_BOTTOM;
+          else if (S(x, y + 1)) fl |= NF_NEQ_TOP;
+        }
+      }
+      I.flags[(size_t)y * nx + x] = fl;
+      if (fl) I.row_plain[y] = 0;
+    }
+  return LBM_OK;
+}
+
+// A(x) = sum_a omega_a G_w(x+e_a) s(x+e_a) e_a on fluid nodes (Eqs. 10, 11, 14)
+static void build_A(const Inst& I, std::vector<double2>& A) {
+  const int nx = I.nx, ny = I.ny;
+  const double cs2 = 1.0 / 3.0;
+  const double scale = I.p.omega == LBM_OMEGA_CS2W ? cs2 : 1.0;
+  A.assign((size_t)nx * ny, make_double2(0.0, 0.0));
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const size_t i = (size_t)y * nx + x;
+      if (I.solid[i]) continue;
+      double ax = 0.0, ay = 0.0;
+      for (int a = 1; a < Q; ++a) {
+        const size_t j = (size_t)wrap(y + EY[a], ny) * nx + wrap(x + EX[a], nx);
+        if (!I.solid[j]) continue;
+        const double w = (a <= 4 ? 1.0 / 3.0 : 1.0 / 12.0) * scale;
+        ax += w * I.gw[j] * EX[a];
+        ay += w * I.gw[j] * EY[a];
+      }
+      A[i] = make_double2(ax, ay);
+    }
+}
+
+template <typename T>
+static void fill_consts(Consts<T>& K, const lbm_params& p, double rho_ref) {
+  const double s_e = 1.0 / p.tau_e, s_z = 1.0 / p.tau_zeta, s_q = 1.0 / p.tau_q;
+  const double G2 = p.G * p.G;
+  K.G = (T)p.G;
+  K.s_e = (T)s_e;
+  K.s_z = (T)s_z;
+  K.s_q = (T)s_q;
+  K.h_e = (T)(1.0 - 0.5 * s_e);
+  K.h_z = (T)(1.0 - 0.5 * s_z);
+  K.h_q = (T)(1.0 - 0.5 * s_q);
+  K.c_e = (T)((1.0 - 0.5 * s_e) * 12.0 * p.sigma * G2 / (p.tau_e - 0.5));
+  K.c_z = (T)((1.0 - 0.5 * s_z) * 12.0 * p.sigma * G2 / (p.tau_zeta - 0.5));
+  K.s_nu = (T)(1.0 / p.tau_nu_L);
+  K.h_nu = (T)(1.0 - 0.5 / p.tau_nu_L);
+  K.tauV = (T)p.tau_nu_V;
+  K.dtau = (T)((p.tau_nu_L - p.tau_nu_V) / (p.rho_L - p.rho_V));
+  K.tau_lo = (T)std::min(p.tau_nu_L, p.tau_nu_V);
+  K.tau_hi = (T)std::max(p.tau_nu_L, p.tau_nu_V);
+  K.rho_V = (T)p.rho_V;
+  K.rho_ref = (T)rho_ref;
+}
+
+static void fill_desc(Inst& I, int prec, int* d_err) {
+  InstDesc& d = I.desc;
+  const lbm_params& p = I.p;
+  d.nx = I.nx;
+  d.ny = I.ny;
+  d.fsi = (int)I.fsi;
+  d.wall = (int)p.wall;
+  d.ghost = (int)p.ghost;
+  d.var_nu = p.tau_nu_L != p.tau_nu_V;
+  d.plane = (long long)I.nx * I.ny;
+  d.f[0] = I.f[0];
+  d.f[1] = I.f[1];
+  d.Fw[0] = I.Fw[0];
+  d.Fw[1] = I.Fw[1];
+  d.flags = I.d_flags;
+  d.row_plain = I.d_row_plain;
+  d.A = I.d_A;
+  d.err = d_err;
+  // Eq. (15) in the form psi^2 = 2 cs^2 / |G| * ((1 - k) rho - c) per branch
+  const double cs2 = 1.0 / 3.0, kV = p.eos_p[0], kM = p.eos_p[1], kL = p.eos_p[2];
+  const double r1 = p.eos_p[3], r2 = p.eos_p[4];
+  const double g = 2.0 * cs2 / (-p.G);
+  d.rho1 = r1;
+  d.rho2 = r2;
+  d.aV = g * (1.0 - kV);
+  d.aM = g * (1.0 - kM);
+  d.bM = -g * (kV - kM) * r1;
+  d.aL = g * (1.0 - kL);
+  d.bL = -g * (kV * r1 + kM * (r2 - r1) - kL * r2);
+  auto split = [](double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+  };
+  const double ab[3][2] = {{d.aV, 0.0}, {d.aM, d.bM}, {d.aL, d.bL}};
+  for (int b = 0; b < 3; ++b) {
+    split(ab[b][0], d.eosf[b][0], d.eosf[b][1]);
+    split(ab[b][1], d.eosf[b][2], d.eosf[b][3]);
+  }
+  split(r1, d.thrf[0], d.thrf[1]);
+  split(r2, d.thrf[2], d.thrf[3]);
+  // the FP32 storage shift is rounded to FP32 so that it is exact in both precisions
+  const double rho_ref = prec == LBM_FP64 ? 0.0 : (double)(float)p.rho_ref;
+  fill_consts<double>(d.cd, p, rho_ref);
+  fill_consts<float>(d.cf, p, rho_ref);
+}
+
+static void free_inst(Inst& I) {
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(I.f[k]);
+    cudaFree(I.Fw[k]);
+    I.f[k] = I.Fw[k] = nullptr;
+  }
+  cudaFree(I.d_flags);
+  cudaFree(I.d_row_plain);
+  cudaFree(I.d_A);
+  I.d_flags = nullptr;
+  I.d_row_plain = nullptr;
+  I.d_A = nullptr;
+}
+
+static void free_ctx(lbm_ctx* c) {
+  if (!c) return;
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  for (auto& I : c->inst) free_inst(I);
+  cudaFree(c->d_desc);
+  cudaFree(c->d_items);
+  cudaFree(c->d_err);
+  cudaFree(c->d_barrier);
+  cudaFree(c->d_rho);
+  cudaFree(c->d_psi);
+  cudaFree(c->d_ux);
+  cudaFree(c->d_uy);
+  diag_free(c->diag);
+  delete c;
+}
+
+static lbm_status upload_inst(lbm_ctx* c, Inst& I) {
+  const size_t N = (size_t)I.nx * I.ny;
+  const size_t ts = tsize(c->prec);
+  for (int k = 0; k < 2; ++k) {
+    CK(cudaMalloc(&I.f[k], Q * N * ts));
+    CK(cudaMemsetAsync(I.f[k], 0, Q * N * ts, c->stream));
+    CK(cudaMalloc(&I.Fw[k], N * 2 * ts));
+    CK(cudaMemsetAsync(I.Fw[k], 0, N * 2 * ts, c->stream));
+  }
+  CK(cudaMalloc(&I.d_flags, N * sizeof(uint16_t)));
+  CK(cudaMemcpy(I.d_flags, I.flags.data(), N * sizeof(uint16_t), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&I.d_row_plain, I.ny));
+  CK(cudaMemcpy(I.d_row_plain, I.row_plain.data(), I.ny, cudaMemcpyHostToDevice));
+  std::vector<double2> A;
+  build_A(I, A);
+  CK(cudaMalloc(&I.d_A, N * sizeof(double2)));
+  CK(cudaMemcpy(I.d_A, A.data(), N * sizeof(double2), cudaMemcpyHostToDevice));
+  return LBM_OK;
+}
+
+// work items: bx-wide column strips, h-row segments
+static lbm_status build_items(lbm_ctx* c) {
+  int bx = c->bx;
+  if (bx <= 0) {
+    // widest instance decides; whole rows up to 512 threads, else 256-wide strips
+    int maxnx = 0;
+    for (auto& I : c->inst) maxnx = std::max(maxnx, I.nx);
+    if (maxnx <= 512) bx = ((maxnx + 31) / 32) * 32;
+    else bx = 256;
+  }
+  bx = std::max(32, std::min(512, ((bx + 31) / 32) * 32));
+  std::vector<WorkItem> items;
+  for (int k = 0; k < (int)c->inst.size(); ++k) {
+    const Inst& I = c->inst[k];
+    int h = c->h;
+    if (h <= 0) h = std::min(I.ny, 64);
+    for (int y0 = 0; y0 < I.ny; y0 += h)
+      for (int x0 = 0; x0 < I.nx; x0 += bx) items.push_back({k, x0, y0, std::min(I.ny, y0 + h)});
+  }
+  cudaFree(c->d_items);
+  c->d_items = nullptr;
+  CK(cudaMalloc(&c->d_items, items.size() * sizeof(WorkItem)));
+  CK(cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+  c->n_items = (int)items.size();
+  c->bx_used = bx;
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  return LBM_OK;
+}
+
+static lbm_status upload_descs(lbm_ctx* c) {
+  std::vector<InstDesc> h(c->inst.size());
+  for (size_t k = 0; k < c->inst.size(); ++k) h[k] = c->inst[k].desc;
+  if (!c->d_desc) CK(cudaMalloc(&c->d_desc, h.size() * sizeof(InstDesc)));
+  CK(cudaMemcpy(c->d_desc, h.data(), h.size() * sizeof(InstDesc), cudaMemcpyHostToDevice));
+  return LBM_OK;
+}
+
+static lbm_status make_inst(const lbm_instance_desc& d, Inst& I) {
+  lbm_status st = validate_params(d.params);
+  if (st != LBM_OK) return st;
+  if (d.nx < 3 || d.ny < 4) return fail(LBM_ERR_ARG, "lattice must be at least 3 x 4 (got %d x %d)", d.nx, d.ny);
+  if ((long long)d.nx * d.ny * Q >= (1LL << 40)) return fail(LBM_ERR_ARG, "lattice too large");
+  if ((int)d.fsi < 0 || (int)d.fsi > 2) return fail(LBM_ERR_ARG, "unknown interaction %d", (int)d.fsi);
+  I.nx = d.nx;
+  I.ny = d.ny;
+  I.p = *d.params;
+  I.fsi = d.fsi;
+  const size_t N = (size_t)d.nx * d.ny;
+  I.solid.assign(N, 0);
+  if (d.solid)
+    for (size_t i = 0; i < N; ++i) I.solid[i] = d.solid[i] != 0;
+  I.gw.assign(N, 0.0);
+  for (size_t i = 0; i < N; ++i)
+    if (I.solid[i]) {
+      I.gw[i] = d.gw_field ? d.gw_field[i] : d.gw_uniform;
+      if (!isfinite(I.gw[i])) return fail(LBM_ERR_ARG, "non-finite G_w at node %zu", i);
+    }
+  return build_flags(I);
+}
+
+extern "C" lbm_status lbm_create_batch(int count, const lbm_instance_desc* descs, void* stream,
+                                       lbm_ctx** out) {
+  if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (count <= 0 || !descs) return fail(LBM_ERR_ARG, "need count > 0 instance descriptors");
+  for (int k = 0; k < count; ++k)
+    if (!descs[k].params) return fail(LBM_ERR_ARG, "instance %d has no params", k);
+  const int prec = (int)descs[0].params->prec;
+  for (int k = 1; k < count; ++k)
+    if ((int)descs[k].params->prec != prec)
+      return fail(LBM_ERR_ARG, "all instances of a batch must share the precision");
+  lbm_ctx* c = new lbm_ctx();
+  c->prec = prec;
+  c->stream = (cudaStream_t)stream;
+  c->inst.resize(count);
+  for (int k = 0; k < count; ++k) {
+    lbm_status st = make_inst(descs[k], c->inst[k]);
+    if (st != LBM_OK) {
+      free_ctx(c);
+      return st;
+    }
+  }
+  lbm_status st = LBM_OK;
+  cudaError_t e = cudaMalloc(&c->d_err, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_barrier, sizeof(unsigned) * 4);
+  if (e == cudaSuccess) e = cudaMemset(c->d_barrier, 0, sizeof(unsigned) * 4);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return fail(LBM_ERR_CUDA, "allocation failed: %s", cudaGetErrorString(e));
+  }
+  for (auto& I : c->inst) {
+    st = upload_inst(c, I);
+    if (st != LBM_OK) break;
+    fill_desc(I, prec, c->d_err);
+  }
+  if (st == LBM_OK) st = upload_descs(c);
+  if (st == LBM_OK) st = build_items(c);
+  if (st == LBM_OK) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "set-up failed: %s", cudaGetErrorString(e));
+  }
+  if (st != LBM_OK) {
+    free_ctx(c);
+    return st;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_create(int nx, int ny, const lbm_params* p, const uint8_t* solid,
+                                 lbm_fsi fsi, const double* gw_field, double gw_uniform,
+                                 void* stream, lbm_ctx** out) {
+  lbm_instance_desc d;
+  d.nx = nx;
+  d.ny = ny;
+  d.params = p;
+  d.solid = solid;
+  d.fsi = fsi;
+  d.gw_field = gw_field;
+  d.gw_uniform = gw_uniform;
+  return lbm_create_batch(1, &d, stream, out);
+}
+
+extern "C" void lbm_destroy(lbm_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  free_ctx(ctx);
+}
+
+extern "C" lbm_status lbm_instance_size(const lbm_ctx* c, int inst, int* nx, int* ny) {
+  if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+  if (inst < 0 || inst >= (int)c->inst.size())
+    return fail(LBM_ERR_ARG, "instance %d out of range [0, %d)", inst, (int)c->inst.size());
+  if (nx) *nx = c->inst[inst].nx;
+  if (ny) *ny = c->inst[inst].ny;
+  return LBM_OK;
+}
+
+static lbm_status check_inst(const lbm_ctx* c, int inst) {
+  if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+  if (inst < 0 || inst >= (int)c->inst.size())
+    return fail(LBM_ERR_ARG, "instance %d out of range [0, %d)", inst, (int)c->inst.size());
+  return LBM_OK;
+}
+
+static lbm_status ensure_scratch(lbm_ctx* c, size_t N) {
+  if (c->scratch_n >= N) return LBM_OK;
+  cudaFree(c->d_rho);
+  cudaFree(c->d_psi);
+  cudaFree(c->d_ux);
+  cudaFree(c->d_uy);
+  c->d_rho = c->d_psi = c->d_ux = c->d_uy = nullptr;
+  c->scratch_n = 0;
+  CK(cudaMalloc(&c->d_rho, N * sizeof(double)));
+  CK(cudaMalloc(&c->d_psi, N * sizeof(double)));
+  CK(cudaMalloc(&c->d_ux, N * sizeof(double)));
+  CK(cudaMalloc(&c->d_uy, N * sizeof(double)));
+  c->scratch_n = N;
+  return LBM_OK;
+}
+
+static lbm_status set_density_dev(lbm_ctx* c, int inst, const double* d_rho0) {
+  Inst& I = c->inst[inst];
+  CK(launch_init(c->prec, I.desc, c->d_desc + inst, c->parity, d_rho0, c->stream));
+  // every instance shares the parity; initialise the other buffer's force too
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_density(lbm_ctx* c, int inst, const double* rho, int src_is_device) {
+  lbm_status st = check_inst(c, inst);
+  if (st != LBM_OK) return st;
+  if (!rho) return fail(LBM_ERR_ARG, "rho is NULL");
+  const size_t N = (size_t)c->inst[inst].nx * c->inst[inst].ny;
+  st = ensure_scratch(c, N);
+  if (st != LBM_OK) return st;
+  CK(cudaMemcpyAsync(c->d_rho, rho, N * sizeof(double),
+                     src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  st = set_density_dev(c, inst, c->d_rho);
+  if (st != LBM_OK) return st;
+  CK(cudaStreamSynchronize(c->stream));
+  c->t = 0;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_init_droplet(lbm_ctx* c, int inst, double x0, double y0, double R,
+                                       double width) {
+  lbm_status st = check_inst(c, inst);
+  if (st != LBM_OK) return st;
+  if (!(width > 0.0) || !(R >= 0.0)) return fail(LBM_ERR_ARG, "need R >= 0 and width > 0");
+  const Inst& I = c->inst[inst];
+  std::vector<double> rho((size_t)I.nx * I.ny);
+  const double rl = I.p.rho_L, rv = I.p.rho_V;
+  for (int y = 0; y < I.ny; ++y)
+    for (int x = 0; x < I.nx; ++x) {
+      double dx = (double)x - x0;
+      dx -= I.nx * floor(dx / I.nx + 0.5);
+      const double dy = (double)y - y0;
+      const double r = sqrt(dx * dx + dy * dy);
+      rho[(size_t)y * I.nx + x] = rv + 0.5 * (rl - rv) * (1.0 - tanh(2.0 * (r - R) / width));
+    }
+  return lbm_set_density(c, inst, rho.data(), 0);
+}
+
+static lbm_status enqueue_steps(lbm_ctx* c, long n) {
+  if (c->persistent) {
+    // one cooperative launch for all n steps; the kernel's error word is
+    // separate from the context's so that a time-out does not hide behind a
+    // stale value
+    CK(cudaMemsetAsync(c->d_barrier + 1, 0, sizeof(unsigned), c->stream));
+    CK(launch_step_persistent(c->prec, c->d_desc, c->d_items, c->n_items, c->parity, n,
+                              c->bx_used, c->d_barrier, c->stream));
+    return LBM_OK;
+  }
+  for (long k = 0; k < n; ++k)
+    CK(launch_step(c->prec, c->d_desc, c->d_items, c->n_items, (int)((c->parity + k) & 1),
+                   c->bx_used, c->stream));
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_step(lbm_ctx* c, long n) {
+  if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+  if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
+  if (n == 0) return LBM_OK;
+  if (c->use_graph && !c->persistent) {
+    auto key = std::make_pair(n, c->parity);
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+      cudaStream_t cap;
+      CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      cudaGraph_t g;
+      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        for (long k = 0; k < n && e == cudaSuccess; ++k)
+          e = launch_step(c->prec, c->d_desc, c->d_items, c->n_items,
+                          (int)((c->parity + k) & 1), c->bx_used, cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess) e = e2;
+      }
+      cudaGraphExec_t ge = nullptr;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+      if (e == cudaSuccess) cudaGraphDestroy(g);
+      cudaStreamDestroy(cap);
+      if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+      it = c->graphs.emplace(key, ge).first;
+    }
+    CK(cudaGraphLaunch(it->second, c->stream));
+  } else {
+    lbm_status st = enqueue_steps(c, n);
+    if (st != LBM_OK) return st;
+  }
+  c->parity = (int)((c->parity + n) & 1);
+  c->t += n;
+  return LBM_OK;
+}
+
+extern "C" long lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
+
+extern "C" lbm_status lbm_sync(lbm_ctx* c) {
+  if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+  CK(cudaStreamSynchronize(c->stream));
+  int h[2] = {0, 0};
+  CK(cudaMemcpy(&h[0], c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&h[1], c->d_barrier + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  const int bits = h[0] | h[1];
+  if (bits & ERR_TIMEOUT)
+    return fail(LBM_ERR_TIMEOUT, "a grid barrier of the persistent step kernel timed out");
+  if (bits & ERR_NONFINITE)
+    return fail(LBM_ERR_NONFINITE, "non-finite or non-positive density on a fluid node");
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_fields(lbm_ctx* c, int inst, double* rho, double* ux, double* uy,
+                                     int dst_is_device) {
+  lbm_status st = check_inst(c, inst);
+  if (st != LBM_OK) return st;
+  const Inst& I = c->inst[inst];
+  const size_t N = (size_t)I.nx * I.ny;
+  st = ensure_scratch(c, N);
+  if (st != LBM_OK) return st;
+  CK(launch_macro(c->prec, I.desc, c->d_desc + inst, c->parity, c->d_rho, c->d_psi,
+                  (ux || uy) ? c->d_ux : nullptr, (ux || uy) ? c->d_uy : nullptr, nullptr,
+                  c->stream));
+  const cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (rho) CK(cudaMemcpyAsync(rho, c->d_rho, N * sizeof(double), k, c->stream));
+  if (ux) CK(cudaMemcpyAsync(ux, c->d_ux, N * sizeof(double), k, c->stream));
+  if (uy) CK(cudaMemcpyAsync(uy, c->d_uy, N * sizeof(double), k, c->stream));
+  return lbm_sync(c);
+}
+
+extern "C" lbm_status lbm_get_populations(lbm_ctx* c, int inst, double* f, int dst_is_device) {
+  lbm_status st = check_inst(c, inst);
+  if (st != LBM_OK) return st;
+  if (!f) return fail(LBM_ERR_ARG, "f is NULL");
+  const Inst& I = c->inst[inst];
+  const size_t N = (size_t)I.nx * I.ny;
+  st = ensure_scratch(c, N);
+  if (st != LBM_OK) return st;
+  double* d_f = nullptr;
+  if (dst_is_device) {
+    d_f = f;
+  } else {
+    CK(cudaMalloc(&d_f, Q * N * sizeof(double)));
+  }
+  cudaError_t e = launch_macro(c->prec, I.desc, c->d_desc + inst, c->parity, c->d_rho, c->d_psi,
+                               nullptr, nullptr, d_f, c->stream);
+  if (e == cudaSuccess && !dst_is_device)
+    e = cudaMemcpyAsync(f, d_f, Q * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (!dst_is_device) cudaFree(d_f);
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "get_populations: %s", cudaGetErrorString(e));
+  return lbm_sync(c);
+}
+
+extern "C" lbm_status lbm_set_gw_field(lbm_ctx* c, int inst, const double* gw) {
+  lbm_status st = check_inst(c, inst);
+  if (st != LBM_OK) return st;
+  if (!gw) return fail(LBM_ERR_ARG, "gw is NULL");
+  Inst& I = c->inst[inst];
+  const size_t N = (size_t)I.nx * I.ny;
+  for (size_t i = 0; i < N; ++i)
+    if (I.solid[i]) {
+      if (!isfinite(gw[i])) return fail(LBM_ERR_ARG, "non-finite G_w at node %zu", i);
+      I.gw[i] = gw[i];
+    }
+  std::vector<double2> A;
+  build_A(I, A);
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(I.d_A, A.data(), N * sizeof(double2), cudaMemcpyHostToDevice));
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_launch(lbm_ctx* c, int bx, int h, int persistent, int graph) {
+  if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+  if (bx < 0 || bx > 512 || h < 0) return fail(LBM_ERR_ARG, "need 0 <= bx <= 512 and h >= 0");
+  CK(cudaStreamSynchronize(c->stream));
+  c->bx = bx;
+  c->h = h;
+  c->persistent = persistent != 0;
+  c->use_graph = graph != 0;
+  return build_items(c);
+}
+
+extern "C" lbm_status lbm_diagnostics(lbm_ctx* c, int inst, double y_w, double x_ref,
+                                      double d_min, lbm_diag* out) {
+  lbm_status st = check_inst(c, inst);
+  if (st != LBM_OK) return st;
+  if (!out) return fail(LBM_ERR_ARG, "out is NULL");
+  const Inst& I = c->inst[inst];
+  const size_t N = (size_t)I.nx * I.ny;
+  st = ensure_scratch(c, N);
+  if (st != LBM_OK) return st;
+  CK(launch_macro(c->prec, I.desc, c->d_desc + inst, c->parity, c->d_rho, c->d_psi, c->d_ux,
+                  c->d_uy, nullptr, c->stream));
+  DiagResult r;
+  CK(run_diagnostics(c->diag, I.nx, I.ny, c->d_rho, c->d_ux, c->d_uy, I.d_flags,
+                     0.5 * (I.p.rho_L + I.p.rho_V), y_w, x_ref, d_min, c->stream, &r));
+  st = lbm_sync(c);
+  memset(out, 0, sizeof *out);
+  out->step = c->t;
+  out->mass = r.mass;
+  out->rho_max = r.rho_max;
+  out->rho_min = r.rho_min;
+  out->u_max = r.u_max;
+  out->theta_deg = r.theta_deg;
+  out->fit_rms = r.fit_rms;
+  out->xc = r.xc;
+  out->yc = r.yc;
+  out->radius = r.radius;
+  out->n_contour = r.n;
+  out->status = st;
+  if (st == LBM_OK && !(isfinite(r.mass) && r.rho_min > 0.0))
+    out->status = st = fail(LBM_ERR_NONFINITE, "non-finite or non-positive density");
+  return st;
+}
+
+extern "C" lbm_status lbm_selftest_wait_timeout(void* stream, double seconds) {
+  if (!(seconds > 0.0 && seconds <= 10.0)) return fail(LBM_ERR_ARG, "seconds must be in (0, 10]");
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned* d = nullptr;
+  CK(cudaMalloc(&d, 4 * sizeof(unsigned)));
+  cudaError_t e = cudaMemsetAsync(d, 0, 4 * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = launch_barrier_selftest(d, (int*)(d + 1), seconds, s);
+  unsigned h[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "selftest: %s", cudaGetErrorString(e));
+  if (h[1] & ERR_TIMEOUT) return fail(LBM_ERR_TIMEOUT, "bounded wait gave up as intended");
+  return LBM_OK;
+}

@@ -1,0 +1,209 @@
+// Diagnostics kernels: density extrema, mass, max |v| and the contact angle
+// (circle fitted to the rho = (rho_L + rho_V)/2 contour, Sec. III.A).
+//
+// Contour points: on every edge between two fluid nodes ((x,y)-(x+1,y) with
+// periodic x, (x,y)-(x,y+1) without crossing the y seam) where rho crosses
+// the level, the linearly interpolated crossing; x is unwrapped about x_ref
+// into [-nx/2, nx/2) and points with y - y_w < d_min are dropped.  The
+// algebraic circle x^2 + y^2 + D x + E y + F = 0 is fitted by least squares;
+// theta = 90 deg + asin((y_c - y_w) / R).
+#include <math.h>
+
+#include "lbm_diag.cuh"
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// crossing on the edge from node i to node j; returns false if none
+__device__ __forceinline__ bool crossing(double ra, double rb, double level, double xa, double ya,
+                                         double dx, double dy, int nx, double x_ref, double y_w,
+                                         double d_min, double& X, double& Y) {
+  if ((ra >= level) == (rb >= level)) return false;
+  const double t = (level - ra) / (rb - ra);
+  X = xa + t * dx - x_ref;
+  X -= nx * floor(X / nx + 0.5);
+  Y = ya + t * dy - y_w;
+  return Y >= d_min;
+}
+
+// mode 0: statistics and fit sums; mode 1: sum of squared radial residuals
+template <int MODE>
+__global__ void __launch_bounds__(DIAG_THREADS)
+    k_diag(int nx, int ny, const double* __restrict__ rho, const double* __restrict__ ux,
+           const double* __restrict__ uy, const uint16_t* __restrict__ flags, double level,
+           double y_w, double x_ref, double d_min, double xc, double yc, double R,
+           double* __restrict__ part) {
+  const long long N = (long long)nx * ny;
+  double acc[DIAG_W];
+#pragma unroll
+  for (int k = 0; k < DIAG_W; ++k) acc[k] = 0.0;
+  acc[1] = -INFINITY;
+  acc[2] = INFINITY;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (flags[i] & NF_SELF_SOLID) continue;
+    const int x = (int)(i % nx), y = (int)(i / nx);
+    const double ra = rho[i];
+    if (MODE == 0) {
+      acc[0] += ra;
+      acc[1] = fmax(acc[1], ra);
+      acc[2] = fmin(acc[2], ra);
+      // a NaN anywhere must surface: fmax/fmin drop NaN, so count it in slot 15
+      if (!(ra == ra)) acc[15] += 1.0;
+      const double u2 = ux[i] * ux[i] + uy[i] * uy[i];
+      acc[3] = fmax(acc[3], u2);
+      if (!(u2 == u2)) acc[15] += 1.0;
+    }
+    for (int dir = 0; dir < 2; ++dir) {
+      long long j;
+      if (dir == 0) {
+        j = (long long)y * nx + (x + 1 == nx ? 0 : x + 1);
+      } else {
+        if (y + 1 >= ny) continue;
+        j = i + nx;
+      }
+      if (flags[j] & NF_SELF_SOLID) continue;
+      double X, Y;
+      if (!crossing(ra, rho[j], level, (double)x, (double)y, dir == 0 ? 1.0 : 0.0,
+                    dir == 0 ? 0.0 : 1.0, nx, x_ref, y_w, d_min, X, Y))
+        continue;
+      if (MODE == 0) {
+        const double r2 = X * X + Y * Y;
+        acc[4] += 1.0;
+        acc[5] += X;
+        acc[6] += Y;
+        acc[7] += X * X;
+        acc[8] += X * Y;
+        acc[9] += Y * Y;
+        acc[10] += X * r2;
+        acc[11] += Y * r2;
+        acc[12] += r2;
+      } else {
+        const double dr = sqrt((X - xc) * (X - xc) + (Y - yc) * (Y - yc)) - R;
+        acc[14] += dr * dr;
+      }
+    }
+  }
+  // block reduction: warp shuffles, then one warp over the warp results
+  __shared__ double sh[DIAG_THREADS / 32][DIAG_W];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < DIAG_W; ++k) {
+    double v = k == 1 ? warp_max(acc[k]) : (k == 2 || k == 3 ? (k == 2 ? warp_min(acc[k]) : warp_max(acc[k])) : warp_sum(acc[k]));
+    if (lane == 0) sh[wid][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < DIAG_W) {
+    const int k = threadIdx.x;
+    double v = sh[0][k];
+    for (int w = 1; w < DIAG_THREADS / 32; ++w) {
+      const double u = sh[w][k];
+      v = k == 1 || k == 3 ? fmax(v, u) : (k == 2 ? fmin(v, u) : v + u);
+    }
+    part[blockIdx.x * DIAG_W + k] = v;
+  }
+}
+
+// fixed-order reduction of the block partials (deterministic)
+__global__ void k_diag_final(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+  const int k = threadIdx.x;
+  if (k >= DIAG_W) return;
+  double v = part[k];
+  for (int b = 1; b < nblocks; ++b) {
+    const double u = part[b * DIAG_W + k];
+    v = k == 1 || k == 3 ? fmax(v, u) : (k == 2 ? fmin(v, u) : v + u);
+  }
+  out[k] = v;
+}
+
+static void solve3(const double A[3][3], const double b[3], double x[3]) {
+  auto det3 = [](const double M[3][3]) {
+    return M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+           M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+           M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+  };
+  const double d = det3(A);
+  for (int c = 0; c < 3; ++c) {
+    double B[3][3];
+    for (int r = 0; r < 3; ++r)
+      for (int k = 0; k < 3; ++k) B[r][k] = (k == c) ? b[r] : A[r][k];
+    x[c] = det3(B) / d;
+  }
+}
+
+cudaError_t diagnostics_into(double* part, double* out, double* h, int nx, int ny,
+                             const double* rho, const double* ux, const double* uy,
+                             const uint16_t* flags, double level, double y_w, double x_ref,
+                             double d_min, cudaStream_t s, DiagResult* r) {
+  const long long N = (long long)nx * ny;
+  int blocks = (int)((N + DIAG_THREADS - 1) / DIAG_THREADS);
+  if (blocks > DIAG_BLOCKS) blocks = DIAG_BLOCKS;
+  k_diag<0><<<blocks, DIAG_THREADS, 0, s>>>(nx, ny, rho, ux, uy, flags, level, y_w, x_ref, d_min,
+                                            0.0, 0.0, 0.0, part);
+  k_diag_final<<<1, 32, 0, s>>>(part, blocks, out);
+  cudaError_t e = cudaMemcpyAsync(h, out, DIAG_W * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  r->mass = h[0];
+  r->rho_max = h[15] > 0 ? NAN : h[1];
+  r->rho_min = h[15] > 0 ? NAN : h[2];
+  r->u_max = h[15] > 0 ? NAN : sqrt(h[3]);
+  r->n = (int)h[4];
+  r->theta_deg = r->fit_rms = r->xc = r->yc = r->radius = NAN;
+  if (r->n < 3) return cudaSuccess;
+  // normal equations of min sum (X^2 + Y^2 + D X + E Y + F)^2
+  const double A[3][3] = {{h[7], h[8], h[5]}, {h[8], h[9], h[6]}, {h[5], h[6], h[4]}};
+  const double b[3] = {-h[10], -h[11], -h[12]};
+  double sol[3];
+  solve3(A, b, sol);
+  const double xc = -0.5 * sol[0], yc = -0.5 * sol[1];
+  const double R = sqrt(xc * xc + yc * yc - sol[2]);
+  double ratio = yc / R;
+  ratio = ratio > 1.0 ? 1.0 : (ratio < -1.0 ? -1.0 : ratio);
+  r->theta_deg = 90.0 + asin(ratio) * (180.0 / M_PI);
+  r->xc = xc + x_ref;
+  r->yc = yc + y_w;
+  r->radius = R;
+  k_diag<1><<<blocks, DIAG_THREADS, 0, s>>>(nx, ny, rho, ux, uy, flags, level, y_w, x_ref, d_min,
+                                            xc, yc, R, part);
+  k_diag_final<<<1, 32, 0, s>>>(part, blocks, out);
+  e = cudaMemcpyAsync(h, out, DIAG_W * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  r->fit_rms = sqrt(h[14] / r->n);
+  return cudaGetLastError();
+}
+
+cudaError_t run_diagnostics(DiagScratch& sc, int nx, int ny, const double* rho, const double* ux,
+                            const double* uy, const uint16_t* flags, double level, double y_w,
+                            double x_ref, double d_min, cudaStream_t s, DiagResult* r) {
+  cudaError_t e = cudaSuccess;
+  if (!sc.d_part) e = cudaMalloc(&sc.d_part, DIAG_BLOCKS * DIAG_W * sizeof(double));
+  if (e == cudaSuccess && !sc.d_out) e = cudaMalloc(&sc.d_out, DIAG_W * sizeof(double));
+  if (e == cudaSuccess && !sc.h_out) e = cudaMallocHost(&sc.h_out, DIAG_W * sizeof(double));
+  if (e != cudaSuccess) return e;
+  return diagnostics_into(sc.d_part, sc.d_out, sc.h_out, nx, ny, rho, ux, uy, flags, level, y_w,
+                          x_ref, d_min, s, r);
+}
+
+void diag_free(DiagScratch& sc) {
+  cudaFree(sc.d_part);
+  cudaFree(sc.d_out);
+  cudaFreeHost(sc.h_out);
+  sc = DiagScratch{};
+}
+
+}  // namespace lbm

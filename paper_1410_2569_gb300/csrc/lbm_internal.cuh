@@ -1,0 +1,91 @@
+// Internal declarations of liblbm (not part of the C ABI).
+//
+// Device data of one lattice instance:
+//   f[2]      two population lattices, [9][ny][nx] of T (double, or float
+//             holding f - w_alpha rho_ref); the step pulls from f[p] and
+//             writes post-collision populations f* to f[p^1].
+//   flags     per node uint16 (bits below); rows whose flags are all zero
+//             are marked plain in row_plain and take the fast path.
+//   A         per node wall vector A(x) = sum_alpha omega_alpha G_w(x+e_alpha)
+//             s(x+e_alpha) e_alpha (zero away from walls); the fluid-solid
+//             force is F_ads = -X(x) A(x) with X = rho, psi or psi^2
+//             (Eqs. (10), (11), (14)).
+//   Fw[2]     per node force of the last collision, read by the wall rule of
+//             Sec. III.A when the next step pulls into a wall node.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm.h"
+
+namespace lbm {
+
+constexpr int Q = 9;
+
+// node flags
+enum : uint16_t {
+  NF_SRC_SOLID = 0x01FF,  // bit a: the pull source x - e_a is solid
+  NF_SELF_SOLID = 1u << 9,
+  NF_NEQ_BOTTOM = 1u << 10,  // fluid, solid directly below, NEQ wall rule
+  NF_NEQ_TOP = 1u << 11,     // fluid, solid directly above, mirrored rule
+  NF_GHOST_UP = 1u << 12,    // solid, fluid directly above (ghost psi source)
+  NF_GHOST_DOWN = 1u << 13,  // solid, fluid directly below
+};
+
+template <typename T>
+struct Consts {
+  T G;                 // Eq. (7)
+  T s_e, s_z, s_q;     // 1/tau_e, 1/tau_zeta, 1/tau_q of Eq. (2)
+  T h_e, h_z, h_q;     // 1 - s/2
+  T c_e, c_z;          // (1 - s/2) * 12 sigma G^2 / (tau - 1/2), Eq. (9)
+  T s_nu, h_nu;        // constant-viscosity rate and 1 - s_nu/2
+  T tauV, dtau, tau_lo, tau_hi;  // tau_nu(rho) = tauV + (rho - rho_V) dtau
+  T rho_V;
+  T rho_ref;           // storage shift (0 in FP64)
+};
+
+struct InstDesc {
+  int nx, ny;
+  int fsi, wall, ghost, var_nu;
+  long long plane;  // nx * ny
+  void* f[2];
+  const uint16_t* flags;
+  const uint8_t* row_plain;
+  const double2* A;
+  void* Fw[2];
+  int* err;  // latched device error bits
+  // Eq. (15) as psi^2 = a rho + b per branch (G < 0, c = 1)
+  double rho1, rho2, aV, aM, bM, aL, bL;
+  // the same as unevaluated FP32 pairs (hi, lo): per branch {a_hi, a_lo,
+  // b_hi, b_lo}; thresholds {rho1_hi, rho1_lo, rho2_hi, rho2_lo}
+  float eosf[3][4];
+  float thrf[4];
+  Consts<double> cd;
+  Consts<float> cf;
+};
+
+struct WorkItem {
+  int inst, x0, y0, y1;
+};
+
+enum : int { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
+
+// D2Q9 weights of the equilibrium
+__host__ __device__ constexpr double w_eq(int a) {
+  return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+// launchers (lbm_kernels.cu)
+cudaError_t launch_step(int prec, const InstDesc* d_inst, const WorkItem* d_items, int n_items,
+                        int parity, int bx, cudaStream_t s);
+cudaError_t launch_step_persistent(int prec, const InstDesc* d_inst, const WorkItem* d_items,
+                                   int n_items, int parity0, long n_steps, int bx,
+                                   unsigned* d_barrier, cudaStream_t s);
+int persistent_max_blocks(int prec, int bx);
+cudaError_t launch_barrier_selftest(unsigned* d_bar, int* d_err, double seconds, cudaStream_t s);
+cudaError_t launch_init(int prec, const InstDesc& h_inst, const InstDesc* d_inst, int parity,
+                        const double* d_rho0, cudaStream_t s);
+cudaError_t launch_macro(int prec, const InstDesc& h_inst, const InstDesc* d_inst, int parity,
+                         double* d_rho, double* d_psi, double* d_ux, double* d_uy, double* d_f,
+                         cudaStream_t s);
+}  // namespace lbm

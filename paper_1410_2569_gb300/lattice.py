@@ -134,8 +134,17 @@ class Lattice:
     def set_launch(self, bx=0, h=0, persistent=False, graph=False):
         check(self._L.lbm_set_launch(self._h, int(bx), int(h), int(persistent), int(graph)))
 
-    def fields(self, inst=0, device=False):
+    def fields(self, inst=0, device=False, out=None):
+        """rho, ux, uy of instance inst: numpy (host) or torch CUDA tensors
+        (device=True); `out` may supply the three host arrays (e.g. pinned)."""
         ny, nx = self.shapes[inst]
+        if out is not None:
+            for k in ("rho", "ux", "uy"):
+                a = out[k]
+                assert a.dtype == np.float64 and a.shape == (ny, nx) and a.flags.c_contiguous
+            check(self._L.lbm_get_fields(self._h, inst, *[out[k].ctypes.data
+                                                          for k in ("rho", "ux", "uy")], 0))
+            return out
         if device:
             import torch
             out = {k: torch.empty((ny, nx), dtype=torch.float64, device="cuda")

@@ -1,0 +1,113 @@
+"""FP32 shifted storage against the FP64 oracle, batched uneven instances,
+the persistent and CUDA-graph launch modes, and device-side error latching."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_1410_2569_gb300 as lbm
+from helpers import gpu_params, run_gpu, run_oracle
+from paper_1410_2569_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_f64"])
+@pytest.mark.parametrize("fsi,gw", [("density", 0.07), ("psi", 1.0), ("modified", 0.1)])
+def test_fp32_density_within_1e4_of_fp64_oracle(cuda, prec, fsi, gw):
+    nx, ny, steps = 100, 60, 1000
+    solid = inputs.flat_walls(nx, ny)
+    drop = (50.0, 0.5, 20.0, 2.0)
+    o = run_oracle(nx, ny, steps, fsi, gw, solid, drop)
+    g = run_gpu(nx, ny, steps, fsi, gw, solid, drop, prec=prec)
+    fo, fg = o.fields(), g.fields()
+    fluid = solid == 0
+    err = np.max(np.abs(fg["rho"][fluid] - fo["rho"][fluid]) / fo["rho"][fluid])
+    assert err <= 1e-4, err
+    du = max(np.max(np.abs(fg["ux"] - fo["ux"])), np.max(np.abs(fg["uy"] - fo["uy"])))
+    assert du <= 1e-4, du
+
+
+def _batch_specs(prec="fp64"):
+    specs = []
+    for k, (fsi, gw, nx, ny) in enumerate([("density", 0.1, 64, 40), ("psi", -1.0, 130, 48),
+                                           ("modified", 0.25, 96, 70), ("modified", -0.1, 33, 20),
+                                           ("density", -0.05, 257, 36)]):
+        specs.append(dict(nx=nx, ny=ny, params=gpu_params(prec=prec), solid=inputs.flat_walls(nx, ny),
+                          fsi=fsi, gw=gw, drop=(nx / 2, 0.5, ny / 3, 2.0)))
+    return specs
+
+
+def _run_batch(specs, steps, launch=None):
+    b = lbm.Lattice([{k: v for k, v in s.items() if k != "drop"} for s in specs])
+    if launch:
+        b.set_launch(**launch)
+    for i, s in enumerate(specs):
+        b.init_droplet(*s["drop"], inst=i)
+    b.step(steps)
+    return b
+
+
+def test_batch_matches_single_instances_bitwise(cuda):
+    specs = _batch_specs()
+    b = _run_batch(specs, 150)
+    for i, s in enumerate(specs):
+        alone = run_gpu(s["nx"], s["ny"], 150, s["fsi"], s["gw"], s["solid"], s["drop"])
+        assert np.array_equal(b.populations(i), alone.populations()), i
+
+
+def test_batch_matches_oracle(cuda):
+    specs = _batch_specs()
+    b = _run_batch(specs, 200)
+    for i, s in enumerate(specs):
+        o = run_oracle(s["nx"], s["ny"], 200, s["fsi"], s["gw"], s["solid"], s["drop"])
+        fluid = s["solid"] == 0
+        gr, orr = b.fields(i)["rho"], o.fields()["rho"]
+        assert np.max(np.abs(gr[fluid] - orr[fluid]) / orr[fluid]) <= 1e-10, i
+
+
+@pytest.mark.parametrize("launch", [dict(persistent=True), dict(graph=True),
+                                    dict(bx=64, h=9, persistent=True)])
+def test_launch_modes_bitwise(cuda, launch):
+    specs = _batch_specs("fp32")
+    ref = _run_batch(specs, 120)
+    got = _run_batch(specs, 120, launch)
+    for i in range(len(specs)):
+        assert np.array_equal(got.populations(i), ref.populations(i)), (i, launch)
+
+
+def test_graph_replay_advances_time(cuda):
+    specs = _batch_specs("fp32")
+    a = _run_batch(specs, 0, dict(graph=True))
+    for _ in range(3):
+        a.step(40)
+    b = _run_batch(specs, 120)
+    assert a.t == 120
+    for i in range(len(specs)):
+        assert np.array_equal(a.populations(i), b.populations(i))
+
+
+def test_nonfinite_is_latched_and_context_recovers(cuda):
+    # tau_nu = 0.6 from a width-2 interface diverges within a few steps
+    nx, ny = 200, 100
+    p = gpu_params(tau_nu_L=0.6, tau_nu_V=0.6)
+    lat = lbm.Lattice.single(nx, ny, p, inputs.flat_walls(nx, ny), "density", -0.14)
+    lat.init_droplet(nx / 2, 0.5, 25.0, 2.0)
+    lat.step(50)
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.sync()
+    assert ei.value.status == 4  # LBM_ERR_NONFINITE
+    # a wider interface is stable; the context stays usable
+    lat2 = lbm.Lattice.single(nx, ny, p, inputs.flat_walls(nx, ny), "density", -0.14)
+    lat2.init_droplet(nx / 2, 0.5, 25.0, 4.0)
+    lat2.step(50)
+    lat2.sync()
+
+
+def test_bounded_wait_gives_up(cuda):
+    L = lbm.load()
+    st = L.lbm_selftest_wait_timeout(None, 0.05)
+    assert st == 5, lbm._lib.STATUS.get(st)  # LBM_ERR_TIMEOUT
+    # the device is still usable afterwards
+    g = run_gpu(40, 20, 10, "modified", 0.1)
+    g.sync()

@@ -197,6 +197,20 @@ def test_fluid_solid_force_at_flat_wall(fsi, omega, factor):
     assert np.abs(dFy[2:ny - 2]).max() == 0.0
 
 
+def test_skip_removes_fluid_fluid_force_next_to_wall():
+    """SKIP (Sec. III.B): at fluid nodes touching solid only F_ads acts."""
+    nx, ny, gw = 16, 12, 0.3
+    solid = inputs.flat_walls(nx, ny)
+    rho = np.full((ny, nx), 3.0)
+    rho[3:8, :] = 300.0
+    o = oracle.Lattice(nx, ny, oracle.paper_params(ghost="skip"), solid, "density", gw)
+    o.set_density(rho)
+    fl = o.fields()
+    assert np.allclose(fl["Fy"][1], 0.5 * gw * rho[1], rtol=1e-14)
+    assert np.abs(fl["Fx"][1]).max() == 0.0
+    assert np.abs(fl["Fy"][2]).max() > 1.0  # Eq. (7) still acts one row up
+
+
 def test_wall_rule_gives_zero_momentum():
     """After the wall rule of Sec. III.A, sum_a e_a f_a + F/2 = 0 at every wall
     node, with F the force of that node's collision."""
