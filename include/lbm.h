@@ -218,6 +218,33 @@ lbm_status lbm_set_launch(lbm_ctx* ctx, int bx, int h, int persistent, int graph
    when the wait gave up as designed; any other status means it did not. */
 lbm_status lbm_selftest_wait_timeout(void* stream, double seconds);
 
+/* Diagnostics without any device allocation, for callers that cannot call
+   cudaMalloc: a host program whose device memory is owned entirely by its
+   own allocator or budget, or a time-critical loop that must not pay the
+   device-wide synchronisation cudaMalloc/cudaFree can imply.  The paper has
+   no counterpart; this is a variant of lbm_diagnostics for fields the
+   caller already holds.
+   Inputs (all device memory, [ny][nx], FP64 unless stated): rho, ux, uy
+   (e.g. from lbm_get_fields with dst_is_device = 1); solid: uint8 mask,
+   nonzero = solid, or NULL for none.  level, y_w, x_ref, d_min as in
+   lbm_diagnostics (level is normally (rho_L + rho_V)/2).  Work is enqueued
+   on `stream` (a cudaStream_t or NULL) and the call waits for it.
+   Scratch: a fixed 77,952-byte device array inside the library, kept by
+   every GPU that loads it until the process exits.  The first call on a
+   device looks up that array's device address (cudaGetSymbolAddress) with
+   the device current; make that first call before any stream capture.  All
+   calls share the array: calls whose work overlaps on a GPU (other streams
+   or threads) race and must be serialised by the caller; each call
+   overwrites all the scratch it reads, so nothing carries over.
+   Limit: nx * ny <= LBM_NOALLOC_MAX_NODES, else LBM_ERR_ARG.  out->step is
+   -1 (no context).  Never calls cudaMalloc, cudaFree or an allocating
+   library routine. */
+#define LBM_NOALLOC_MAX_NODES (1LL << 28)
+lbm_status lbm_diagnostics_noalloc(int nx, int ny, const double* rho, const double* ux,
+                                   const double* uy, const uint8_t* solid, double level,
+                                   double y_w, double x_ref, double d_min, void* stream,
+                                   lbm_diag* out);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* lbm_last_error(void);
 

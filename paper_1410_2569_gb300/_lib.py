@@ -17,7 +17,8 @@ STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
 EXPORTS = ["lbm_default_params", "lbm_create", "lbm_create_batch", "lbm_destroy",
            "lbm_instance_size", "lbm_init_droplet", "lbm_set_density", "lbm_step", "lbm_sync",
            "lbm_time", "lbm_get_fields", "lbm_get_populations", "lbm_diagnostics",
-           "lbm_set_gw_field", "lbm_set_launch", "lbm_selftest_wait_timeout", "lbm_last_error"]
+           "lbm_set_gw_field", "lbm_set_launch", "lbm_selftest_wait_timeout",
+           "lbm_diagnostics_noalloc", "lbm_last_error"]
 
 
 class LbmParams(ctypes.Structure):
@@ -88,6 +89,7 @@ def load(path=LIB_PATH):
         "lbm_set_gw_field": (i, [vp, i, vp]),
         "lbm_set_launch": (i, [vp, i, i, i, i]),
         "lbm_selftest_wait_timeout": (i, [vp, d]),
+        "lbm_diagnostics_noalloc": (i, [i, i, vp, vp, vp, vp, d, d, d, d, vp, P(LbmDiag)]),
         "lbm_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():

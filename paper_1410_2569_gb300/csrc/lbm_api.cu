@@ -39,6 +39,16 @@ static lbm_status fail(lbm_status s, const char* fmt, ...) {
 
 extern "C" const char* lbm_last_error(void) { return g_err.c_str(); }
 
+lbm_status lbm::set_error(lbm_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
 namespace {
 
 struct Inst {

@@ -8,7 +8,11 @@
 // algebraic circle x^2 + y^2 + D x + E y + F = 0 is fitted by least squares;
 // theta = 90 deg + asin((y_c - y_w) / R).
 #include <math.h>
+#include <string.h>
 
+#include <mutex>
+
+#include "lbm.h"
 #include "lbm_diag.cuh"
 #include "lbm_internal.cuh"
 
@@ -39,11 +43,20 @@ __device__ __forceinline__ bool crossing(double ra, double rb, double level, dou
   return Y >= d_min;
 }
 
+// solid test of node i: the library's node flags, or a plain 0/1 mask
+// (NULL = no solid node)
+__device__ __forceinline__ bool is_solid(const uint16_t* flags, long long i) {
+  return (flags[i] & NF_SELF_SOLID) != 0;
+}
+__device__ __forceinline__ bool is_solid(const uint8_t* mask, long long i) {
+  return mask != nullptr && mask[i] != 0;
+}
+
 // mode 0: statistics and fit sums; mode 1: sum of squared radial residuals
-template <int MODE>
+template <int MODE, typename MaskT>
 __global__ void __launch_bounds__(DIAG_THREADS)
     k_diag(int nx, int ny, const double* __restrict__ rho, const double* __restrict__ ux,
-           const double* __restrict__ uy, const uint16_t* __restrict__ flags, double level,
+           const double* __restrict__ uy, const MaskT* __restrict__ flags, double level,
            double y_w, double x_ref, double d_min, double xc, double yc, double R,
            double* __restrict__ part) {
   const long long N = (long long)nx * ny;
@@ -54,7 +67,7 @@ __global__ void __launch_bounds__(DIAG_THREADS)
   acc[2] = INFINITY;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
-    if (flags[i] & NF_SELF_SOLID) continue;
+    if (is_solid(flags, i)) continue;
     const int x = (int)(i % nx), y = (int)(i / nx);
     const double ra = rho[i];
     if (MODE == 0) {
@@ -75,7 +88,7 @@ __global__ void __launch_bounds__(DIAG_THREADS)
         if (y + 1 >= ny) continue;
         j = i + nx;
       }
-      if (flags[j] & NF_SELF_SOLID) continue;
+      if (is_solid(flags, j)) continue;
       double X, Y;
       if (!crossing(ra, rho[j], level, (double)x, (double)y, dir == 0 ? 1.0 : 0.0,
                     dir == 0 ? 0.0 : 1.0, nx, x_ref, y_w, d_min, X, Y))
@@ -144,15 +157,17 @@ static void solve3(const double A[3][3], const double b[3], double x[3]) {
   }
 }
 
-cudaError_t diagnostics_into(double* part, double* out, double* h, int nx, int ny,
-                             const double* rho, const double* ux, const double* uy,
-                             const uint16_t* flags, double level, double y_w, double x_ref,
-                             double d_min, cudaStream_t s, DiagResult* r) {
+template <typename MaskT>
+static cudaError_t diagnostics_into_t(double* part, double* out, double* h, int nx, int ny,
+                                      const double* rho, const double* ux, const double* uy,
+                                      const MaskT* flags, double level, double y_w,
+                                      double x_ref, double d_min, cudaStream_t s,
+                                      DiagResult* r) {
   const long long N = (long long)nx * ny;
   int blocks = (int)((N + DIAG_THREADS - 1) / DIAG_THREADS);
   if (blocks > DIAG_BLOCKS) blocks = DIAG_BLOCKS;
-  k_diag<0><<<blocks, DIAG_THREADS, 0, s>>>(nx, ny, rho, ux, uy, flags, level, y_w, x_ref, d_min,
-                                            0.0, 0.0, 0.0, part);
+  k_diag<0, MaskT><<<blocks, DIAG_THREADS, 0, s>>>(nx, ny, rho, ux, uy, flags, level, y_w,
+                                                   x_ref, d_min, 0.0, 0.0, 0.0, part);
   k_diag_final<<<1, 32, 0, s>>>(part, blocks, out);
   cudaError_t e = cudaMemcpyAsync(h, out, DIAG_W * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -177,14 +192,22 @@ cudaError_t diagnostics_into(double* part, double* out, double* h, int nx, int n
   r->xc = xc + x_ref;
   r->yc = yc + y_w;
   r->radius = R;
-  k_diag<1><<<blocks, DIAG_THREADS, 0, s>>>(nx, ny, rho, ux, uy, flags, level, y_w, x_ref, d_min,
-                                            xc, yc, R, part);
+  k_diag<1, MaskT><<<blocks, DIAG_THREADS, 0, s>>>(nx, ny, rho, ux, uy, flags, level, y_w,
+                                                   x_ref, d_min, xc, yc, R, part);
   k_diag_final<<<1, 32, 0, s>>>(part, blocks, out);
   e = cudaMemcpyAsync(h, out, DIAG_W * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
   r->fit_rms = sqrt(h[14] / r->n);
   return cudaGetLastError();
+}
+
+cudaError_t diagnostics_into(double* part, double* out, double* h, int nx, int ny,
+                             const double* rho, const double* ux, const double* uy,
+                             const uint16_t* flags, double level, double y_w, double x_ref,
+                             double d_min, cudaStream_t s, DiagResult* r) {
+  return diagnostics_into_t<uint16_t>(part, out, h, nx, ny, rho, ux, uy, flags, level, y_w, x_ref,
+                                      d_min, s, r);
 }
 
 cudaError_t run_diagnostics(DiagScratch& sc, int nx, int ny, const double* rho, const double* ux,
@@ -207,3 +230,85 @@ void diag_free(DiagScratch& sc) {
 }
 
 }  // namespace lbm
+
+// ---------------------------------------------------------------------------
+// Diagnostics without allocation (lbm_diagnostics_noalloc).
+//
+// The block partials and the reduced result live in one file-scope device
+// array instead of memory obtained from cudaMalloc.  Host code cannot use the
+// array's name as a device address, so the first call on each device looks
+// the address up with cudaGetSymbolAddress (with that device current) and
+// keeps it; every later call on that device reuses it.  Each call overwrites
+// every partial it reads, so nothing needs clearing between calls, but all
+// calls on a device share the array: calls whose kernels overlap on the GPU
+// (other streams, other host threads) race and must be serialised by the
+// caller.
+// ---------------------------------------------------------------------------
+namespace lbm {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static __device__ __align__(256) double g_noalloc_scratch[DIAG_BLOCKS * DIAG_W + DIAG_W];
+static double* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mu;
+
+static cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace lbm
+
+extern "C" lbm_status lbm_diagnostics_noalloc(int nx, int ny, const double* rho,
+                                              const double* ux, const double* uy,
+                                              const uint8_t* solid, double level, double y_w,
+                                              double x_ref, double d_min, void* stream,
+                                              lbm_diag* out) {
+  using namespace lbm;
+  if (!out) return set_error(LBM_ERR_ARG, "lbm_diagnostics_noalloc: out is NULL");
+  memset(out, 0, sizeof *out);
+  if (!rho || !ux || !uy)
+    return set_error(LBM_ERR_ARG, "lbm_diagnostics_noalloc: rho, ux and uy are required");
+  if (nx < 1 || ny < 1 || (long long)nx * ny > LBM_NOALLOC_MAX_NODES)
+    return set_error(LBM_ERR_ARG,
+                     "lbm_diagnostics_noalloc: nx * ny must be in [1, %lld] (got %d x %d)",
+                     (long long)LBM_NOALLOC_MAX_NODES, nx, ny);
+  double* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess)
+    return set_error(LBM_ERR_CUDA, "lbm_diagnostics_noalloc: scratch address: %s",
+                     cudaGetErrorString(e));
+  double h[DIAG_W];
+  DiagResult r;
+  e = diagnostics_into_t<uint8_t>(scratch, scratch + DIAG_BLOCKS * DIAG_W, h, nx, ny, rho, ux, uy,
+                                  solid, level, y_w, x_ref, d_min, (cudaStream_t)stream, &r);
+  if (e != cudaSuccess)
+    return set_error(LBM_ERR_CUDA, "lbm_diagnostics_noalloc: %s", cudaGetErrorString(e));
+  out->step = -1;
+  out->mass = r.mass;
+  out->rho_max = r.rho_max;
+  out->rho_min = r.rho_min;
+  out->u_max = r.u_max;
+  out->theta_deg = r.theta_deg;
+  out->fit_rms = r.fit_rms;
+  out->xc = r.xc;
+  out->yc = r.yc;
+  out->radius = r.radius;
+  out->n_contour = r.n;
+  out->status = LBM_OK;
+  if (!(r.mass == r.mass) || !(r.rho_min > 0.0)) {
+    out->status = LBM_ERR_NONFINITE;
+    return set_error(LBM_ERR_NONFINITE, "lbm_diagnostics_noalloc: non-finite or non-positive density");
+  }
+  return LBM_OK;
+}

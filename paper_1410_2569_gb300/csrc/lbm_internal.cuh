@@ -75,6 +75,9 @@ __host__ __device__ constexpr double w_eq(int a) {
   return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
+// records the calling thread's lbm_last_error() message and returns s
+lbm_status set_error(lbm_status s, const char* fmt, ...);
+
 // launchers (lbm_kernels.cu)
 cudaError_t launch_step(int prec, const InstDesc* d_inst, const WorkItem* d_items, int n_items,
                         int parity, int bx, cudaStream_t s);
