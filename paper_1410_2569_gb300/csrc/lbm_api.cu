@@ -340,22 +340,29 @@ static lbm_status upload_inst(lbm_ctx* c, Inst& I) {
 
 // work items: bx-wide column strips, h-row segments
 static lbm_status build_items(lbm_ctx* c) {
+  // a block of bx threads covers bx - 2 columns (its two edge lanes evaluate
+  // the halo columns)
   int bx = c->bx;
   if (bx <= 0) {
     // widest instance decides; whole rows up to 512 threads, else 256-wide strips
     int maxnx = 0;
     for (auto& I : c->inst) maxnx = std::max(maxnx, I.nx);
-    if (maxnx <= 512) bx = ((maxnx + 31) / 32) * 32;
+    if (maxnx + 2 <= 512) bx = ((maxnx + 2 + 31) / 32) * 32;
     else bx = 256;
   }
   bx = std::max(32, std::min(512, ((bx + 31) / 32) * 32));
+  const int cols = bx - 2;
   std::vector<WorkItem> items;
   for (int k = 0; k < (int)c->inst.size(); ++k) {
     const Inst& I = c->inst[k];
     int h = c->h;
-    if (h <= 0) h = std::min(I.ny, 64);
+    if (h <= 0) {
+      // segments of at most 64 rows, balanced
+      const int nseg = (I.ny + 63) / 64;
+      h = (I.ny + nseg - 1) / nseg;
+    }
     for (int y0 = 0; y0 < I.ny; y0 += h)
-      for (int x0 = 0; x0 < I.nx; x0 += bx) items.push_back({k, x0, y0, std::min(I.ny, y0 + h)});
+      for (int x0 = 0; x0 < I.nx; x0 += cols) items.push_back({k, x0, y0, std::min(I.ny, y0 + h)});
   }
   cudaFree(c->d_items);
   c->d_items = nullptr;
