@@ -206,11 +206,18 @@ lbm_status lbm_diagnostics(lbm_ctx* ctx, int inst, double y_w, double x_ref, dou
    nodes) and rebuilds the wall vectors of the fluid-solid force. */
 lbm_status lbm_set_gw_field(lbm_ctx* ctx, int inst, const double* gw);
 
-/* Launch shape of lbm_step: bx threads per block along x, h rows per block
-   (0 = choose automatically), persistent = 1 runs all n steps in one
-   cooperative launch with a bounded grid barrier between steps,
-   graph = 1 captures the n per-step launches in a CUDA graph. */
-lbm_status lbm_set_launch(lbm_ctx* ctx, int bx, int h, int persistent, int graph);
+/* Launch shape of lbm_step: bx threads per block along x (a block covers
+   bx - 2 columns), h rows per block (0 = choose automatically),
+   persistent = 1 runs all n steps in one cooperative launch with a bounded
+   grid barrier between steps, graph = 1 captures the n per-step launches in
+   a CUDA graph.  stages selects the step pipeline: 1 = blocks marching up
+   rows with loads prefetched into registers; 2 = independent warps, each
+   marching up a 30-column strip (no block barriers; persistent is ignored);
+   8 or 16 = blocks marching up rows with a TMA ring of that many source rows
+   in shared memory (FP32 storage, every lattice width a multiple of 4);
+   0 = automatic (warp strips).  Results do not depend on any of these
+   choices. */
+lbm_status lbm_set_launch(lbm_ctx* ctx, int bx, int h, int persistent, int graph, int stages);
 
 /* Self-test of the bounded device-side wait used by the persistent step
    kernel's grid barrier: one block waits for an arrival that never comes and

@@ -87,7 +87,7 @@ def load(path=LIB_PATH):
         "lbm_get_populations": (i, [vp, i, vp, i]),
         "lbm_diagnostics": (i, [vp, i, d, d, d, P(LbmDiag)]),
         "lbm_set_gw_field": (i, [vp, i, vp]),
-        "lbm_set_launch": (i, [vp, i, i, i, i]),
+        "lbm_set_launch": (i, [vp, i, i, i, i, i]),
         "lbm_selftest_wait_timeout": (i, [vp, d]),
         "lbm_diagnostics_noalloc": (i, [i, i, vp, vp, vp, vp, d, d, d, d, vp, P(LbmDiag)]),
         "lbm_last_error": (ctypes.c_char_p, []),

@@ -81,8 +81,8 @@ struct lbm_ctx {
   unsigned* d_barrier = nullptr;  // [0] arrival counter, [1] error word of the persistent kernel
   int parity = 0;
   long t = 0;
-  int bx = 0, h = 0, persistent = 0, use_graph = 0;
-  int bx_used = 0;
+  int bx = 0, h = 0, persistent = 0, use_graph = 0, stages = 0;
+  int bx_used = 0, stages_used = 0;
   // CUDA graphs of n launches, keyed by (n, parity)
   std::map<std::pair<long, int>, cudaGraphExec_t> graphs;
   // scratch for field read-back and diagnostics
@@ -340,8 +340,9 @@ static lbm_status upload_inst(lbm_ctx* c, Inst& I) {
 
 // work items: bx-wide column strips, h-row segments
 static lbm_status build_items(lbm_ctx* c) {
-  // a block of bx threads covers bx - 2 columns (its two edge lanes evaluate
-  // the halo columns)
+  // block rows: a block of bx threads covers bx - 2 columns (its two edge
+  // lanes evaluate the halo columns); warp strips: each warp covers 30
+  const bool warp_mode = c->stages == 2 || c->stages == 0;
   int bx = c->bx;
   if (bx <= 0) {
     // widest instance decides; whole rows up to 512 threads, else 256-wide strips
@@ -350,15 +351,18 @@ static lbm_status build_items(lbm_ctx* c) {
     if (maxnx + 2 <= 512) bx = ((maxnx + 2 + 31) / 32) * 32;
     else bx = 256;
   }
-  bx = std::max(32, std::min(512, ((bx + 31) / 32) * 32));
-  const int cols = bx - 2;
+  if (warp_mode && c->bx <= 0) bx = 256;
+  bx = std::max(32, std::min(warp_mode ? 256 : 512, ((bx + 31) / 32) * 32));
+  const int cols = warp_mode ? 30 : bx - 2;
   std::vector<WorkItem> items;
   for (int k = 0; k < (int)c->inst.size(); ++k) {
     const Inst& I = c->inst[k];
     int h = c->h;
     if (h <= 0) {
-      // segments of at most 64 rows, balanced
-      const int nseg = (I.ny + 63) / 64;
+      // balanced segments of at most 64 rows (32 for warp strips: more,
+      // shorter strips balance the waves better)
+      const int hmax = warp_mode ? 32 : 64;
+      const int nseg = (I.ny + hmax - 1) / hmax;
       h = (I.ny + nseg - 1) / nseg;
     }
     for (int y0 = 0; y0 < I.ny; y0 += h)
@@ -370,6 +374,17 @@ static lbm_status build_items(lbm_ctx* c) {
   CK(cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
   c->n_items = (int)items.size();
   c->bx_used = bx;
+  // TMA pipeline: FP32 storage, every lattice width a multiple of 4
+  bool tma_ok = c->prec != LBM_FP64;
+  for (auto& I : c->inst) tma_ok = tma_ok && (I.nx % 4 == 0);
+  int S = c->stages == 0 ? 8 : c->stages;
+  // the ring must fit the per-block shared-memory limit; the pipeline needs
+  // at least 8 stages (rows y-1..y+2 in use while later rows are in flight)
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  while (S >= 8 && tma_smem_bytes(bx, S) > (size_t)optin) S /= 2;
+  c->stages_used = warp_mode ? PIPE_WARP : ((tma_ok && c->stages != 1 && S >= 8) ? S : 0);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   c->graphs.clear();
   return LBM_OK;
@@ -551,18 +566,18 @@ extern "C" lbm_status lbm_init_droplet(lbm_ctx* c, int inst, double x0, double y
 }
 
 static lbm_status enqueue_steps(lbm_ctx* c, long n) {
-  if (c->persistent) {
+  if (c->persistent && c->stages_used != PIPE_WARP) {
     // one cooperative launch for all n steps; the kernel's error word is
     // separate from the context's so that a time-out does not hide behind a
     // stale value
     CK(cudaMemsetAsync(c->d_barrier + 1, 0, sizeof(unsigned), c->stream));
     CK(launch_step_persistent(c->prec, c->d_desc, c->d_items, c->n_items, c->parity, n,
-                              c->bx_used, c->d_barrier, c->stream));
+                              c->bx_used, c->stages_used, c->d_barrier, c->stream));
     return LBM_OK;
   }
   for (long k = 0; k < n; ++k)
     CK(launch_step(c->prec, c->d_desc, c->d_items, c->n_items, (int)((c->parity + k) & 1),
-                   c->bx_used, c->stream));
+                   c->bx_used, c->stages_used, c->stream));
   return LBM_OK;
 }
 
@@ -581,7 +596,7 @@ extern "C" lbm_status lbm_step(lbm_ctx* c, long n) {
       if (e == cudaSuccess) {
         for (long k = 0; k < n && e == cudaSuccess; ++k)
           e = launch_step(c->prec, c->d_desc, c->d_items, c->n_items,
-                          (int)((c->parity + k) & 1), c->bx_used, cap);
+                          (int)((c->parity + k) & 1), c->bx_used, c->stages_used, cap);
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e == cudaSuccess) e = e2;
       }
@@ -678,14 +693,19 @@ extern "C" lbm_status lbm_set_gw_field(lbm_ctx* c, int inst, const double* gw) {
   return LBM_OK;
 }
 
-extern "C" lbm_status lbm_set_launch(lbm_ctx* c, int bx, int h, int persistent, int graph) {
+extern "C" lbm_status lbm_set_launch(lbm_ctx* c, int bx, int h, int persistent, int graph,
+                                      int stages) {
   if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
   if (bx < 0 || bx > 512 || h < 0) return fail(LBM_ERR_ARG, "need 0 <= bx <= 512 and h >= 0");
+  if (!(stages == 0 || stages == 1 || stages == 2 || stages == 8 || stages == 16))
+    return fail(LBM_ERR_ARG, "stages must be 0 (automatic), 1 (block rows), 2 (warp strips), "
+                             "8 or 16 (TMA ring)");
   CK(cudaStreamSynchronize(c->stream));
   c->bx = bx;
   c->h = h;
   c->persistent = persistent != 0;
   c->use_graph = graph != 0;
+  c->stages = stages;
   return build_items(c);
 }
 

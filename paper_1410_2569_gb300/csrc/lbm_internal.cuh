@@ -44,7 +44,7 @@ struct Consts {
   T rho_ref;           // storage shift (0 in FP64)
 };
 
-struct InstDesc {
+struct __align__(16) InstDesc {
   int nx, ny;
   int fsi, wall, ghost, var_nu;
   long long plane;  // nx * ny
@@ -70,21 +70,28 @@ struct WorkItem {
 
 enum : int { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
 
+// step pipelines (launch_step's `stages` argument): block rows with register
+// prefetch, warp strips, or block rows with a TMA ring of 8 / 16 stages
+enum : int { PIPE_BLOCK = 0, PIPE_WARP = 2 };
+
 // D2Q9 weights of the equilibrium
 __host__ __device__ constexpr double w_eq(int a) {
   return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
+
+// shared memory of the TMA-pipelined FP32 step for bx threads and S stages
+size_t tma_smem_bytes(int bx, int S);
 
 // records the calling thread's lbm_last_error() message and returns s
 lbm_status set_error(lbm_status s, const char* fmt, ...);
 
 // launchers (lbm_kernels.cu)
 cudaError_t launch_step(int prec, const InstDesc* d_inst, const WorkItem* d_items, int n_items,
-                        int parity, int bx, cudaStream_t s);
+                        int parity, int bx, int stages, cudaStream_t s);
 cudaError_t launch_step_persistent(int prec, const InstDesc* d_inst, const WorkItem* d_items,
-                                   int n_items, int parity0, long n_steps, int bx,
+                                   int n_items, int parity0, long n_steps, int bx, int stages,
                                    unsigned* d_barrier, cudaStream_t s);
-int persistent_max_blocks(int prec, int bx);
+int persistent_max_blocks(int prec, int bx, int stages);
 cudaError_t launch_barrier_selftest(unsigned* d_bar, int* d_err, double seconds, cudaStream_t s);
 cudaError_t launch_init(int prec, const InstDesc& h_inst, const InstDesc* d_inst, int parity,
                         const double* d_rho0, cudaStream_t s);

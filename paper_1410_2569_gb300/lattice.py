@@ -131,8 +131,9 @@ class Lattice:
     def sync(self):
         check(self._L.lbm_sync(self._h))
 
-    def set_launch(self, bx=0, h=0, persistent=False, graph=False):
-        check(self._L.lbm_set_launch(self._h, int(bx), int(h), int(persistent), int(graph)))
+    def set_launch(self, bx=0, h=0, persistent=False, graph=False, stages=0):
+        check(self._L.lbm_set_launch(self._h, int(bx), int(h), int(persistent), int(graph),
+                                     int(stages)))
 
     def fields(self, inst=0, device=False, out=None):
         """rho, ux, uy of instance inst: numpy (host) or torch CUDA tensors

@@ -67,7 +67,8 @@ def test_batch_matches_oracle(cuda):
 
 
 @pytest.mark.parametrize("launch", [dict(persistent=True), dict(graph=True),
-                                    dict(bx=64, h=9, persistent=True)])
+                                    dict(bx=64, h=9, persistent=True), dict(stages=2),
+                                    dict(stages=2, bx=64, h=11), dict(stages=2, graph=True)])
 def test_launch_modes_bitwise(cuda, launch):
     specs = _batch_specs("fp32")
     ref = _run_batch(specs, 120)
@@ -111,3 +112,47 @@ def test_bounded_wait_gives_up(cuda):
     # the device is still usable afterwards
     g = run_gpu(40, 20, 10, "modified", 0.1)
     g.sync()
+
+
+def _batch_specs_w4(prec="fp32"):
+    # every width a multiple of 4: the TMA row pipeline applies
+    specs = []
+    for fsi, gw, nx, ny in [("density", 0.1, 64, 40), ("psi", -1.0, 132, 48),
+                            ("modified", 0.25, 96, 70), ("modified", -0.1, 36, 20),
+                            ("density", -0.05, 252, 36)]:
+        specs.append(dict(nx=nx, ny=ny, params=gpu_params(prec=prec),
+                          solid=inputs.flat_walls(nx, ny), fsi=fsi, gw=gw,
+                          drop=(nx / 2, 0.5, ny / 3, 2.0)))
+    return specs
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_f64"])
+@pytest.mark.parametrize("launch", [dict(stages=8), dict(stages=16, bx=128),
+                                    dict(stages=8, bx=32, h=5), dict(stages=8, persistent=True),
+                                    dict(stages=8, bx=64, h=7, persistent=True),
+                                    dict(stages=2), dict(stages=2, bx=256, h=3), dict(stages=2, bx=32, h=2)])
+def test_tma_pipeline_bitwise_equal_to_register_pipeline(cuda, prec, launch):
+    specs = _batch_specs_w4(prec)
+    ref = _run_batch(specs, 130, dict(stages=1))
+    got = _run_batch(specs, 130, launch)
+    for i in range(len(specs)):
+        assert np.array_equal(got.populations(i), ref.populations(i)), (i, launch)
+
+
+def test_tma_pipeline_bounce_back_pillars(cuda):
+    nx, ny = 92, 60
+    solid = inputs.pillars(nx, ny, height=10, width=6, gap=3)
+    drop = (45.0, 30.0, 15.0, 2.0)
+    a = run_gpu(nx, ny, 300, "modified", 0.3, solid, drop, launch=dict(stages=1), prec="fp32",
+                wall="bb", ghost="skip")
+    b = run_gpu(nx, ny, 300, "modified", 0.3, solid, drop, launch=dict(stages=8, bx=64, h=9),
+                prec="fp32", wall="bb", ghost="skip")
+    assert np.array_equal(a.populations(), b.populations())
+
+
+def test_fp64_warp_strips_bitwise(cuda):
+    specs = _batch_specs("fp64")
+    ref = _run_batch(specs, 90, dict(stages=1))
+    got = _run_batch(specs, 90, dict(stages=2, bx=96, h=13))
+    for i in range(len(specs)):
+        assert np.array_equal(got.populations(i), ref.populations(i)), i
