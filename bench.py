@@ -32,6 +32,34 @@ FALLBACK_HBM_GBS = 6800.0
 # (504 G FP64 instructions/s; 1.008 TFLOP/s counting an FMA as 2 flops)
 FP64_OPS_PER_S = 504e9
 BYTES_PER_NODE = {"fp32": 72.0, "fp32_f64": 72.0, "fp64": 144.0}
+KERNEL_SRC = os.path.join(ROOT, "paper_1410_2569_gb300", "csrc", "lbm_kernels.cu")
+PROFILE = os.path.join(ROOT, "profiles", "step_kernel_sweep.md")
+
+
+def kernel_sha():
+    import hashlib
+    with open(KERNEL_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()
+
+
+def profile_figures():
+    """Per-launch counters of the step kernels from the committed ncu summary
+    (lines `key: value`), or {} when that summary was taken on a different
+    kernel source than the one built now."""
+    try:
+        with open(PROFILE) as fh:
+            kv = dict(ln.strip("`* \n").split(": ", 1) for ln in fh if ": " in ln)
+    except OSError:
+        return {}
+    if kv.get("kernel-source-sha256", "").strip() != kernel_sha():
+        return {}
+    out = {}
+    for k, v in kv.items():
+        try:
+            out[k] = float(v.split()[0])
+        except (ValueError, IndexError):
+            pass
+    return out
 
 
 def sweep_instances(prec):
@@ -157,7 +185,8 @@ def run_ours(args, ws, rank, local):
     nodes = len(inputs.sweep_cases()) * NX * NY
     results = {}
     y_w = inputs.wall_height("copy")
-    for prec in ("fp32", "fp64"):
+    precs = ("fp32", "fp64") if args.prec == "both" else (args.prec,)
+    for prec in precs:
         insts = sweep_instances(prec)
         lat = lbm.Lattice(insts, stream=stream)
         for k in range(len(insts)):
@@ -188,7 +217,7 @@ def run_ours(args, ws, rank, local):
     # end-to-end through the C ABI with host buffers: host density fields in,
     # `chunk` steps, host rho/ux/uy fields out, per e2e iteration
     e2e = None
-    if rank == 0 or ws > 1:
+    if not args.no_e2e and "fp32" in results:
         lat = results["fp32"]["lat"]
         n_inst = len(inputs.sweep_cases())
         host_rho = torch.empty((NY, NX), dtype=torch.float64).pin_memory().numpy()
@@ -212,21 +241,27 @@ def run_ours(args, ws, rank, local):
                "steps_per_call": chunk}
     for r in results.values():
         r.pop("lat", None)
-    if rank != 0:
+    if rank != 0 or args.prec != "both":
         if dist:
             dist.destroy_process_group()
+        if rank == 0:
+            print(json.dumps({k: {kk: vv for kk, vv in v.items() if kk != "clocks"}
+                              for k, v in results.items()}))
         return
     hbm, peak_kind = measured_peaks()
     f32, f64 = results["fp32"], results["fp64"]
+    prof = profile_figures()
 
     def roof(prec, dt, steps):
         achieved = nodes * BYTES_PER_NODE[prec] * steps / dt / 1e9  # per GPU
         return achieved
     ach32 = roof("fp32", f32["dt"], args.steps)
     ach64 = roof("fp64", f64["dt"], args.steps)
-    # FP64 step: FP64 instructions per node counted from the source arithmetic
-    # (pull + density 8, psi ~12, collision ~120); FP64-pipe bound on this GPU
-    fp64_ops_node = 140.0
+    # FP64 step: FP64-pipe instructions per node counted by ncu
+    # (smsp__inst_executed_pipe_fp64 x 32 / nodes) in the committed profile,
+    # else the count from the source arithmetic (density 8, psi ~12,
+    # collision ~120)
+    fp64_ops_node = prof.get("fp64_pipe_thread_ops_per_node", 140.0)
     fp64_alu = nodes * fp64_ops_node * args.steps / f64["dt"] / 1e9
     cpu = cpu_baseline(args) if not args.no_cpu else None
     line = {
@@ -248,7 +283,8 @@ def run_ours(args, ws, rank, local):
                    "l2": "inputs larger than L2 (415 MB FP32 populations), no flush",
                    "parallelism": f"independent sweeps per GPU x{ws}"},
         "roofline": {"bound": "hbm", "achieved": round(ach32, 1), "peak": hbm,
-                     "unit": "GB/s", "frac": round(ach32 / hbm, 4), "traffic": None,
+                     "unit": "GB/s", "frac": round(ach32 / hbm, 4),
+                     "traffic": prof.get("fp32_dram_bytes_per_launch"),
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_node": BYTES_PER_NODE["fp32"]},
         "fp64": {"value": round(f64["mlups"], 2), "unit": "MLUPS",
@@ -335,6 +371,9 @@ def main():
     ap.add_argument("--launch", default="", help="bx,h,persistent,graph")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--prec", default="both", choices=["both", "fp32", "fp64"],
+                    help="a single precision prints only its timings (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
