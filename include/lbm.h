@@ -206,6 +206,22 @@ lbm_status lbm_diagnostics(lbm_ctx* ctx, int inst, double y_w, double x_ref, dou
    nodes) and rebuilds the wall vectors of the fluid-solid force. */
 lbm_status lbm_set_gw_field(lbm_ctx* ctx, int inst, const double* gw);
 
+/* Gradient of a contact-angle loss with respect to the G_w field, by a
+   hand-written reverse mode of the FP64 time step (every stage of Sec. II:
+   Eqs. (5)-(7), (9)-(11), (14), (15), the wall rule of Sec. III.A).
+   Runs T steps from the context's current state (leaving it T steps
+   later), measures theta as lbm_diagnostics does (circle fitted to the
+   (rho_L + rho_V)/2 contour, points below y_w + d_min dropped, x unwrapped
+   about x_ref), sets *loss_out = (theta - theta_target)^2 (deg^2) and
+   *theta_out = theta, and writes dL/dG_w into grad_gw ([ny][nx] host
+   array, nonzero on solid nodes only).  The loss is differentiated with the
+   set of contour edges held fixed (it is smooth while no edge changes
+   sides).  Memory: checkpoints of the state every ceil(sqrt(T)) steps plus
+   one recomputed segment, O(sqrt(T) * nx * ny).  Needs a single-lattice
+   LBM_FP64 context with tau_nu_L == tau_nu_V; synchronises. */
+lbm_status lbm_adjoint(lbm_ctx* ctx, long T, double theta_target, double y_w, double x_ref,
+                       double d_min, double* loss_out, double* theta_out, double* grad_gw);
+
 /* Launch shape of lbm_step: bx threads per block along x (a block covers
    bx - 2 columns), h rows per block (0 = choose automatically),
    persistent = 1 runs all n steps in one cooperative launch with a bounded

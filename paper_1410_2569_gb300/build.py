@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm.so")
-SOURCES = ["lbm_kernels.cu", "lbm_diag.cu", "lbm_api.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_diag.cu", "lbm_adjoint.cu", "lbm_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -250,6 +250,7 @@ static void fill_desc(Inst& I, int prec, int* d_err) {
   d.wall = (int)p.wall;
   d.ghost = (int)p.ghost;
   d.var_nu = p.tau_nu_L != p.tau_nu_V;
+  d.omega_cs2w = p.omega == LBM_OMEGA_CS2W;
   d.plane = (long long)I.nx * I.ny;
   d.f[0] = I.f[0];
   d.f[1] = I.f[1];
@@ -755,5 +756,237 @@ extern "C" lbm_status lbm_selftest_wait_timeout(void* stream, double seconds) {
   cudaFree(d);
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "selftest: %s", cudaGetErrorString(e));
   if (h[1] & ERR_TIMEOUT) return fail(LBM_ERR_TIMEOUT, "bounded wait gave up as intended");
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// lbm_adjoint: loss L = (theta - theta_target)^2 after T steps and dL/dG_w.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Crossing {
+  long long ia, ib;  // edge end nodes
+  double dx, dy;     // edge direction (1,0) or (0,1)
+  double X, Y;       // point relative to (x_ref, y_w)
+};
+
+// the contact-angle fit of lbm_diagnostics on a host density field, with
+// dtheta/drho over the fixed set of crossing edges
+static bool fit_with_gradient(int nx, int ny, const std::vector<double>& rho,
+                              const std::vector<uint8_t>& solid, double level, double y_w,
+                              double x_ref, double d_min, double* theta, std::vector<double>* dth) {
+  std::vector<Crossing> pts;
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const long long i = (long long)y * nx + x;
+      if (solid[i]) continue;
+      for (int dir = 0; dir < 2; ++dir) {
+        const int x2 = dir == 0 ? x + 1 : x, y2 = dir == 0 ? y : y + 1;
+        if (dir == 1 && y2 >= ny) continue;
+        const long long j = (long long)y2 * nx + (x2 % nx);
+        if (solid[j]) continue;
+        const double ra = rho[i], rb = rho[j];
+        if ((ra >= level) == (rb >= level)) continue;
+        const double t = (level - ra) / (rb - ra);
+        double X = (double)x + t * (x2 - x) - x_ref;
+        X -= nx * floor(X / nx + 0.5);
+        const double Y = (double)y + t * (y2 - y) - y_w;
+        if (Y < d_min) continue;
+        pts.push_back({i, j, (double)(x2 - x), (double)(y2 - y), X, Y});
+      }
+    }
+  if (pts.size() < 3) return false;
+  double M[3][3] = {{0}}, r[3] = {0};
+  for (auto& q : pts) {
+    const double u[3] = {q.X, q.Y, 1.0}, z = q.X * q.X + q.Y * q.Y;
+    for (int a = 0; a < 3; ++a) {
+      for (int c = 0; c < 3; ++c) M[a][c] += u[a] * u[c];
+      r[a] -= u[a] * z;
+    }
+  }
+  auto det3 = [](const double A[3][3]) {
+    return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+           A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+           A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+  };
+  auto solve = [&](const double b[3], double x[3]) {
+    const double d = det3(M);
+    for (int c = 0; c < 3; ++c) {
+      double B[3][3];
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) B[i][k] = k == c ? b[i] : M[i][k];
+      x[c] = det3(B) / d;
+    }
+  };
+  double p[3];
+  solve(r, p);
+  const double xc = -0.5 * p[0], yc = -0.5 * p[1];
+  const double R = sqrt(xc * xc + yc * yc - p[2]);
+  double s = yc / R;
+  s = s > 1.0 ? 1.0 : (s < -1.0 ? -1.0 : s);
+  *theta = 90.0 + asin(s) * (180.0 / M_PI);
+  if (!dth) return true;
+  // dtheta/dp for p = (D, E, F), yc = -E/2, R^2 = D^2/4 + E^2/4 - F
+  const double dths = (180.0 / M_PI) / sqrt(fmax(1e-300, 1.0 - s * s));
+  const double R3 = R * R * R;
+  const double g[3] = {dths * (yc * xc) / (2.0 * R3), dths * (-(R * R - yc * yc) / (2.0 * R3)),
+                       dths * (yc / (2.0 * R3))};
+  double mu[3];
+  solve(g, mu);  // M is symmetric
+  dth->assign(rho.size(), 0.0);
+  for (auto& q : pts) {
+    const double u[3] = {q.X, q.Y, 1.0}, z = q.X * q.X + q.Y * q.Y;
+    const double mu_u = mu[0] * u[0] + mu[1] * u[1] + mu[2];
+    const double u_p = u[0] * p[0] + u[1] * p[1] + p[2];
+    // from M p = r: dtheta = mu . (dr - dM p)
+    const double dX = -mu[0] * z - 2.0 * q.X * mu_u - mu[0] * u_p - mu_u * p[0];
+    const double dY = -mu[1] * z - 2.0 * q.Y * mu_u - mu[1] * u_p - mu_u * p[1];
+    const double ra = rho[q.ia], rb = rho[q.ib], den = (rb - ra) * (rb - ra);
+    const double dt_a = (level - rb) / den, dt_b = (ra - level) / den;
+    const double dpt = dX * q.dx + dY * q.dy;
+    (*dth)[q.ia] += dpt * dt_a;
+    (*dth)[q.ib] += dpt * dt_b;
+  }
+  return true;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { cudaFree(p); }
+};
+
+}  // namespace
+
+extern "C" lbm_status lbm_adjoint(lbm_ctx* c, long T, double theta_target, double y_w,
+                                  double x_ref, double d_min, double* loss_out,
+                                  double* theta_out, double* grad_gw) {
+  if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+  if (c->inst.size() != 1) return fail(LBM_ERR_ARG, "lbm_adjoint needs a single-lattice context");
+  if (c->prec != LBM_FP64) return fail(LBM_ERR_ARG, "lbm_adjoint needs LBM_FP64");
+  if (T < 1) return fail(LBM_ERR_ARG, "T must be >= 1");
+  Inst& I = c->inst[0];
+  if (I.p.tau_nu_L != I.p.tau_nu_V)
+    return fail(LBM_ERR_ARG, "lbm_adjoint needs tau_nu_L == tau_nu_V");
+  const size_t N = (size_t)I.nx * I.ny;
+  const size_t fN = Q * N;
+  lbm_status st = ensure_scratch(c, N);
+  if (st != LBM_OK) return st;
+  CK(cudaStreamSynchronize(c->stream));
+  const int saved_persistent = c->persistent;
+  c->persistent = 0;
+  // checkpoints every k steps: the library state (f*, F at walls) and parity
+  const long k = (long)ceil(sqrt((double)T));
+  const long nck = (T + k - 1) / k;
+  DevBuf ck, seg, lamA, lamB, grad, scr;
+  const size_t ck_one = (fN + 2 * N) * sizeof(double);
+  CK(cudaMalloc(&ck.p, nck * ck_one));
+  CK(cudaMalloc(&seg.p, (size_t)k * fN * sizeof(double)));
+  CK(cudaMalloc(&lamA.p, fN * sizeof(double)));
+  CK(cudaMalloc(&lamB.p, fN * sizeof(double)));
+  CK(cudaMalloc(&grad.p, N * sizeof(double)));
+  CK(cudaMemsetAsync(grad.p, 0, N * sizeof(double), c->stream));
+  // scratch of the reverse step
+  const size_t scr_doubles = 3 * N + fN + 2 * N + fN + 2 * N + 2 * N + 2 * N;
+  CK(cudaMalloc(&scr.p, scr_doubles * sizeof(double)));
+  AdjScratch S;
+  {
+    double* q = (double*)scr.p;
+    S.rho = q; q += N;
+    S.psi = q; q += N;
+    S.dpsi = q; q += N;
+    S.lamp = q; q += fN;
+    S.lamF_bc = (double2*)q; q += 2 * N;
+    S.lam_dir = q; q += fN;
+    S.lam_g = (double2*)q; q += 2 * N;
+    S.lam_A = (double2*)q; q += 2 * N;
+    S.lam_psi_loc = q; q += N;
+    S.lam_rho_loc = q; q += N;
+  }
+  const size_t fbytes = fN * sizeof(double), Fbytes = 2 * N * sizeof(double);
+  std::vector<int> ck_parity(nck);
+  auto save = [&](long ci) -> lbm_status {
+    char* dst = (char*)ck.p + ci * ck_one;
+    CK(cudaMemcpyAsync(dst, I.f[c->parity], fbytes, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(dst + fbytes, I.Fw[c->parity], Fbytes, cudaMemcpyDeviceToDevice, c->stream));
+    ck_parity[ci] = c->parity;
+    return LBM_OK;
+  };
+  auto restore = [&](long ci) -> lbm_status {
+    const char* srcp = (const char*)ck.p + ci * ck_one;
+    c->parity = ck_parity[ci];
+    CK(cudaMemcpyAsync(I.f[c->parity], srcp, fbytes, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(I.Fw[c->parity], srcp + fbytes, Fbytes, cudaMemcpyDeviceToDevice, c->stream));
+    return LBM_OK;
+  };
+  const long t0 = c->t;
+  // forward pass with checkpoints
+  for (long ci = 0; ci < nck; ++ci) {
+    if ((st = save(ci)) != LBM_OK) return st;
+    if ((st = lbm_step(c, std::min(k, T - ci * k))) != LBM_OK) return st;
+  }
+  st = lbm_sync(c);
+  if (st != LBM_OK) return st;
+  const int final_parity = c->parity;
+  const long final_t = c->t;
+  // loss and its seed dL/df(T) = dL/drho(T) on every population
+  std::vector<double> rho(N);
+  CK(launch_macro(c->prec, I.desc, c->d_desc, c->parity, c->d_rho, c->d_psi, nullptr, nullptr,
+                  nullptr, c->stream));
+  CK(cudaMemcpyAsync(rho.data(), c->d_rho, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  double theta = 0.0;
+  std::vector<double> dth;
+  if (!fit_with_gradient(I.nx, I.ny, rho, I.solid, 0.5 * (I.p.rho_L + I.p.rho_V), y_w, x_ref,
+                         d_min, &theta, &dth)) {
+    c->persistent = saved_persistent;
+    return fail(LBM_ERR_STATE, "fewer than 3 contour points: no contact angle");
+  }
+  const double L = (theta - theta_target) * (theta - theta_target);
+  std::vector<double> seed(fN, 0.0);
+  for (size_t i = 0; i < N; ++i)
+    for (int a = 0; a < Q; ++a) seed[a * N + i] = 2.0 * (theta - theta_target) * dth[i];
+  CK(cudaMemcpyAsync(lamA.p, seed.data(), fbytes, cudaMemcpyHostToDevice, c->stream));
+  // save the final state, then run the segments backwards
+  DevBuf fin;
+  CK(cudaMalloc(&fin.p, ck_one));
+  CK(cudaMemcpyAsync(fin.p, I.f[final_parity], fbytes, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync((char*)fin.p + fbytes, I.Fw[final_parity], Fbytes, cudaMemcpyDeviceToDevice,
+                     c->stream));
+  double* lam_next = (double*)lamA.p;
+  double* lam_cur = (double*)lamB.p;
+  for (long ci = nck - 1; ci >= 0; --ci) {
+    const long len = std::min(k, T - ci * k);
+    if ((st = restore(ci)) != LBM_OK) return st;
+    // recompute f(t) for the segment
+    for (long s = 0; s < len; ++s) {
+      double* fs = (double*)seg.p + s * fN;
+      CK(launch_macro(c->prec, I.desc, c->d_desc, c->parity, c->d_rho, c->d_psi, nullptr,
+                      nullptr, fs, c->stream));
+      if ((st = lbm_step(c, 1)) != LBM_OK) return st;
+    }
+    for (long s = len - 1; s >= 0; --s) {
+      const double* fs = (const double*)seg.p + s * fN;
+      CK(launch_adjoint_step(I.desc, c->d_desc, fs, lam_next, lam_cur, (double*)grad.p, S,
+                             c->stream));
+      std::swap(lam_next, lam_cur);
+    }
+  }
+  // back to the state after the forward pass
+  c->parity = final_parity;
+  CK(cudaMemcpyAsync(I.f[final_parity], fin.p, fbytes, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(I.Fw[final_parity], (char*)fin.p + fbytes, Fbytes, cudaMemcpyDeviceToDevice,
+                     c->stream));
+  c->t = final_t;
+  c->persistent = saved_persistent;
+  (void)t0;
+  if (grad_gw)
+    CK(cudaMemcpyAsync(grad_gw, grad.p, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  st = lbm_sync(c);
+  if (st != LBM_OK) return st;
+  if (grad_gw)
+    for (size_t i = 0; i < N; ++i)
+      if (!I.solid[i]) grad_gw[i] = 0.0;
+  if (loss_out) *loss_out = L;
+  if (theta_out) *theta_out = theta;
   return LBM_OK;
 }

@@ -47,6 +47,8 @@ struct Consts {
 struct __align__(16) InstDesc {
   int nx, ny;
   int fsi, wall, ghost, var_nu;
+  int omega_cs2w;   // omega_alpha = cs^2 w_alpha (else w_alpha) in A(x)
+  int pad_;
   long long plane;  // nx * ny
   void* f[2];
   const uint16_t* flags;
@@ -81,6 +83,19 @@ __host__ __device__ constexpr double w_eq(int a) {
 
 // shared memory of the TMA-pipelined FP32 step for bx threads and S stages
 size_t tma_smem_bytes(int bx, int S);
+
+// scratch of one reverse step (lbm_adjoint.cu), FP64, N nodes
+struct AdjScratch {
+  double *rho = nullptr, *psi = nullptr, *dpsi = nullptr;
+  double* lamp = nullptr;  // [9][N]
+  double2* lamF_bc = nullptr;
+  double* lam_dir = nullptr;  // [9][N]
+  double2 *lam_g = nullptr, *lam_A = nullptr;
+  double *lam_psi_loc = nullptr, *lam_rho_loc = nullptr;
+};
+cudaError_t launch_adjoint_step(const InstDesc& h, const InstDesc* d_inst, const double* f,
+                                const double* lam_next, double* lam_out, double* grad,
+                                AdjScratch& s, cudaStream_t st);
 
 // records the calling thread's lbm_last_error() message and returns s
 lbm_status set_error(lbm_status s, const char* fmt, ...);

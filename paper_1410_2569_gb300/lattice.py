@@ -177,3 +177,17 @@ class Lattice:
     def set_gw_field(self, gw, inst=0):
         g = np.ascontiguousarray(gw, dtype=np.float64)
         check(self._L.lbm_set_gw_field(self._h, inst, g.ctypes.data))
+
+    def adjoint(self, T, theta_target, y_w=0.5, x_ref=None, d_min=3.0, want_grad=True):
+        """T steps from the current state, loss (theta - theta_target)^2 and its
+        gradient with respect to the G_w field (lbm_adjoint).  Returns
+        (loss, theta, grad[ny][nx] or None)."""
+        ny, nx = self.shapes[0]
+        loss = ctypes.c_double()
+        theta = ctypes.c_double()
+        grad = np.zeros((ny, nx)) if want_grad else None
+        check(self._L.lbm_adjoint(self._h, int(T), float(theta_target), float(y_w),
+                                  float(nx / 2 if x_ref is None else x_ref), float(d_min),
+                                  ctypes.byref(loss), ctypes.byref(theta),
+                                  None if grad is None else grad.ctypes.data))
+        return loss.value, theta.value, grad
