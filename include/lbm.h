@@ -225,8 +225,9 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, long T, double theta_target, double y_w, do
 /* Launch shape of lbm_step: bx threads per block along x (a block covers
    bx - 2 columns), h rows per block (0 = choose automatically),
    persistent = 1 runs all n steps in one cooperative launch with a bounded
-   grid barrier between steps, graph = 1 captures the n per-step launches in
-   a CUDA graph.  stages selects the step pipeline: 1 = blocks marching up
+   grid barrier between steps, graph = 1 captures the n per-step launches (or
+   the one persistent launch) in a CUDA graph, reused for every later call
+   with the same n.  stages selects the step pipeline: 1 = blocks marching up
    rows with loads prefetched into registers; 2 = independent warps, each
    marching up a 30-column strip (no block barriers; persistent is ignored);
    8 or 16 = blocks marching up rows with a TMA ring of that many source rows
@@ -234,6 +235,25 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, long T, double theta_target, double y_w, do
    0 = automatic (warp strips).  Results do not depend on any of these
    choices. */
 lbm_status lbm_set_launch(lbm_ctx* ctx, int bx, int h, int persistent, int graph, int stages);
+
+/* Writes the state of every lattice (post-collision populations, wall
+   forces, step counter) to `path`, with a hash of the lattices, parameters,
+   masks and G_w fields.  Synchronises. */
+lbm_status lbm_save(lbm_ctx* ctx, const char* path);
+
+/* Restores a state written by lbm_save into a context created with the same
+   lattices, parameters, masks and G_w fields (LBM_ERR_ARG otherwise).
+   Stepping on from the loaded state is bitwise identical to never having
+   stopped. */
+lbm_status lbm_load(lbm_ctx* ctx, const char* path);
+
+/* Times lbm_step over `steps` steps for a fixed list of launch shapes
+   (pipeline, block width, rows per block) on the context's own lattices and
+   keeps the fastest.  The state and the step counter are restored after
+   every trial, so the call changes nothing but the launch shape; results do
+   not depend on the shape.  Outputs (any may be NULL): the chosen bx, h and
+   stages (as in lbm_set_launch) and its time per step in ms. */
+lbm_status lbm_autotune(lbm_ctx* ctx, int steps, int* bx, int* h, int* stages, double* ms);
 
 /* Self-test of the bounded device-side wait used by the persistent step
    kernel's grid barrier: one block waits for an arrival that never comes and

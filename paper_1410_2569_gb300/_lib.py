@@ -18,7 +18,8 @@ EXPORTS = ["lbm_default_params", "lbm_create", "lbm_create_batch", "lbm_destroy"
            "lbm_instance_size", "lbm_init_droplet", "lbm_set_density", "lbm_step", "lbm_sync",
            "lbm_time", "lbm_get_fields", "lbm_get_populations", "lbm_diagnostics",
            "lbm_set_gw_field", "lbm_set_launch", "lbm_selftest_wait_timeout",
-           "lbm_diagnostics_noalloc", "lbm_adjoint", "lbm_last_error"]
+           "lbm_diagnostics_noalloc", "lbm_adjoint", "lbm_save", "lbm_load", "lbm_autotune",
+           "lbm_last_error"]
 
 
 class LbmParams(ctypes.Structure):
@@ -90,6 +91,9 @@ def load(path=LIB_PATH):
         "lbm_set_launch": (i, [vp, i, i, i, i, i]),
         "lbm_selftest_wait_timeout": (i, [vp, d]),
         "lbm_adjoint": (i, [vp, l, d, d, d, d, P(d), P(d), vp]),
+        "lbm_save": (i, [vp, ctypes.c_char_p]),
+        "lbm_load": (i, [vp, ctypes.c_char_p]),
+        "lbm_autotune": (i, [vp, i, P(i), P(i), P(i), P(d)]),
         "lbm_diagnostics_noalloc": (i, [i, i, vp, vp, vp, vp, d, d, d, d, vp, P(LbmDiag)]),
         "lbm_last_error": (ctypes.c_char_p, []),
     }

@@ -586,7 +586,7 @@ extern "C" lbm_status lbm_step(lbm_ctx* c, long n) {
   if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
   if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
   if (n == 0) return LBM_OK;
-  if (c->use_graph && !c->persistent) {
+  if (c->use_graph) {
     auto key = std::make_pair(n, c->parity);
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
@@ -595,9 +595,17 @@ extern "C" lbm_status lbm_step(lbm_ctx* c, long n) {
       cudaGraph_t g;
       cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        for (long k = 0; k < n && e == cudaSuccess; ++k)
-          e = launch_step(c->prec, c->d_desc, c->d_items, c->n_items,
-                          (int)((c->parity + k) & 1), c->bx_used, c->stages_used, cap);
+        if (c->persistent && c->stages_used != PIPE_WARP) {
+          // one persistent launch for all n steps, captured once
+          e = cudaMemsetAsync(c->d_barrier + 1, 0, sizeof(unsigned), cap);
+          if (e == cudaSuccess)
+            e = launch_step_persistent(c->prec, c->d_desc, c->d_items, c->n_items, c->parity, n,
+                                       c->bx_used, c->stages_used, c->d_barrier, cap);
+        } else {
+          for (long k = 0; k < n && e == cudaSuccess; ++k)
+            e = launch_step(c->prec, c->d_desc, c->d_items, c->n_items,
+                            (int)((c->parity + k) & 1), c->bx_used, c->stages_used, cap);
+        }
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e == cudaSuccess) e = e2;
       }
@@ -988,5 +996,202 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, long T, double theta_target, doubl
       if (!I.solid[i]) grad_gw[i] = 0.0;
   if (loss_out) *loss_out = L;
   if (theta_out) *theta_out = theta;
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume and the launch-shape autotuner.
+// ---------------------------------------------------------------------------
+namespace {
+
+// FNV-1a over the bytes that define an instance
+static uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+static uint64_t ctx_hash(const lbm_ctx* c) {
+  uint64_t h = 1469598103934665603ull;
+  h = fnv(h, &c->prec, sizeof c->prec);
+  for (const auto& I : c->inst) {
+    h = fnv(h, &I.nx, sizeof I.nx);
+    h = fnv(h, &I.ny, sizeof I.ny);
+    h = fnv(h, &I.fsi, sizeof I.fsi);
+    // parameters field by field (no padding bytes)
+    const lbm_params& p = I.p;
+    const double dv[] = {p.eos_p[0], p.eos_p[1], p.eos_p[2], p.eos_p[3], p.eos_p[4], p.G,
+                         p.sigma, p.tau_rho, p.tau_e, p.tau_zeta, p.tau_j, p.tau_q, p.tau_nu_L,
+                         p.tau_nu_V, p.rho_L, p.rho_V, p.rho_ref};
+    const int iv[] = {(int)p.eos, (int)p.wall, (int)p.ghost, (int)p.omega, (int)p.prec};
+    h = fnv(h, dv, sizeof dv);
+    h = fnv(h, iv, sizeof iv);
+    h = fnv(h, I.solid.data(), I.solid.size());
+    h = fnv(h, I.gw.data(), I.gw.size() * sizeof(double));
+  }
+  return h;
+}
+
+const char kMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', '1'};
+
+}  // namespace
+
+extern "C" lbm_status lbm_save(lbm_ctx* c, const char* path) {
+  if (!c || !path) return fail(LBM_ERR_ARG, "ctx and path are required");
+  lbm_status st = lbm_sync(c);
+  if (st != LBM_OK) return st;
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return fail(LBM_ERR_ARG, "cannot open %s for writing", path);
+  const uint64_t h = ctx_hash(c);
+  const int64_t hdr[4] = {(int64_t)c->inst.size(), (int64_t)c->t, (int64_t)c->parity,
+                          (int64_t)c->prec};
+  bool ok = fwrite(kMagic, 1, 8, fp) == 8 && fwrite(&h, sizeof h, 1, fp) == 1 &&
+            fwrite(hdr, sizeof hdr, 1, fp) == 1;
+  std::vector<char> buf;
+  for (auto& I : c->inst) {
+    if (!ok) break;
+    const size_t N = (size_t)I.nx * I.ny, ts = tsize(c->prec);
+    const size_t fb = Q * N * ts, Fb = 2 * N * ts;
+    buf.resize(fb + Fb);
+    cudaError_t e = cudaMemcpy(buf.data(), I.f[c->parity], fb, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(buf.data() + fb, I.Fw[c->parity], Fb, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      fclose(fp);
+      return fail(LBM_ERR_CUDA, "lbm_save: %s", cudaGetErrorString(e));
+    }
+    ok = fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+  }
+  ok = (fclose(fp) == 0) && ok;
+  return ok ? LBM_OK : fail(LBM_ERR_ARG, "lbm_save: write to %s failed", path);
+}
+
+extern "C" lbm_status lbm_load(lbm_ctx* c, const char* path) {
+  if (!c || !path) return fail(LBM_ERR_ARG, "ctx and path are required");
+  CK(cudaStreamSynchronize(c->stream));
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return fail(LBM_ERR_ARG, "cannot open %s", path);
+  char magic[8];
+  uint64_t h = 0;
+  int64_t hdr[4];
+  bool ok = fread(magic, 1, 8, fp) == 8 && memcmp(magic, kMagic, 8) == 0 &&
+            fread(&h, sizeof h, 1, fp) == 1 && fread(hdr, sizeof hdr, 1, fp) == 1;
+  if (!ok || h != ctx_hash(c) || hdr[0] != (int64_t)c->inst.size() || hdr[3] != c->prec ||
+      (hdr[2] != 0 && hdr[2] != 1)) {
+    fclose(fp);
+    return fail(LBM_ERR_ARG, "lbm_load: %s was not saved from a context with these lattices, "
+                             "parameters, masks and G_w", path);
+  }
+  std::vector<char> buf;
+  const int parity = (int)hdr[2];
+  for (auto& I : c->inst) {
+    const size_t N = (size_t)I.nx * I.ny, ts = tsize(c->prec);
+    const size_t fb = Q * N * ts, Fb = 2 * N * ts;
+    buf.resize(fb + Fb);
+    if (fread(buf.data(), 1, buf.size(), fp) != buf.size()) {
+      fclose(fp);
+      return fail(LBM_ERR_ARG, "lbm_load: %s is truncated", path);
+    }
+    cudaError_t e = cudaMemcpy(I.f[parity], buf.data(), fb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(I.Fw[parity], buf.data() + fb, Fb, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      fclose(fp);
+      return fail(LBM_ERR_CUDA, "lbm_load: %s", cudaGetErrorString(e));
+    }
+  }
+  fclose(fp);
+  c->parity = parity;
+  c->t = (long)hdr[1];
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_autotune(lbm_ctx* c, int steps, int* bx_out, int* h_out,
+                                   int* stages_out, double* ms_out) {
+  if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+  if (steps < 1) return fail(LBM_ERR_ARG, "steps must be >= 1");
+  lbm_status st = lbm_sync(c);
+  if (st != LBM_OK) return st;
+  // keep the state: every trial starts from it and it is put back at the end
+  std::vector<void*> keep;
+  auto cleanup = [&]() {
+    for (void* p : keep) cudaFree(p);
+  };
+  for (auto& I : c->inst) {
+    const size_t N = (size_t)I.nx * I.ny, ts = tsize(c->prec);
+    void *pf = nullptr, *pF = nullptr;
+    if (cudaMalloc(&pf, Q * N * ts) != cudaSuccess || cudaMalloc(&pF, 2 * N * ts) != cudaSuccess) {
+      cudaFree(pf);
+      cleanup();
+      return fail(LBM_ERR_OOM, "lbm_autotune: no room for a copy of the state");
+    }
+    keep.push_back(pf);
+    keep.push_back(pF);
+    cudaMemcpy(pf, I.f[c->parity], Q * N * ts, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(pF, I.Fw[c->parity], 2 * N * ts, cudaMemcpyDeviceToDevice);
+  }
+  const int parity0 = c->parity;
+  const long t0 = c->t;
+  auto put_back = [&]() {
+    c->parity = parity0;
+    c->t = t0;
+    for (size_t k = 0; k < c->inst.size(); ++k) {
+      auto& I = c->inst[k];
+      const size_t N = (size_t)I.nx * I.ny, ts = tsize(c->prec);
+      cudaMemcpy(I.f[parity0], keep[2 * k], Q * N * ts, cudaMemcpyDeviceToDevice);
+      cudaMemcpy(I.Fw[parity0], keep[2 * k + 1], 2 * N * ts, cudaMemcpyDeviceToDevice);
+    }
+  };
+  struct Cand {
+    int bx, h, stages;
+  };
+  std::vector<Cand> cands = {{256, 16, 2}, {256, 25, 2}, {256, 32, 2}, {256, 48, 2},
+                             {128, 25, 2}, {128, 32, 2}, {224, 32, 1}, {224, 50, 1},
+                             {416, 50, 1}, {224, 50, 8}, {416, 50, 8}};
+  const int saved[5] = {c->bx, c->h, c->persistent, c->use_graph, c->stages};
+  c->persistent = 0;
+  c->use_graph = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e300;
+  Cand bestc = cands[0];
+  for (const Cand& q : cands) {
+    c->bx = q.bx;
+    c->h = q.h;
+    c->stages = q.stages;
+    if (build_items(c) != LBM_OK) continue;
+    if (q.stages >= 8 && c->stages_used < 8) continue;  // TMA not applicable here
+    put_back();
+    if (lbm_step(c, 2) != LBM_OK) continue;
+    cudaEventRecord(e0, c->stream);
+    if (lbm_step(c, steps) != LBM_OK) continue;
+    cudaEventRecord(e1, c->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bestc = q;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  put_back();
+  c->bx = bestc.bx;
+  c->h = bestc.h;
+  c->stages = bestc.stages;
+  c->persistent = saved[2];
+  c->use_graph = saved[3];
+  st = build_items(c);
+  cleanup();
+  if (st != LBM_OK) return st;
+  st = lbm_sync(c);
+  if (st != LBM_OK) return st;
+  if (bx_out) *bx_out = bestc.bx;
+  if (h_out) *h_out = bestc.h;
+  if (stages_out) *stages_out = bestc.stages;
+  if (ms_out) *ms_out = best / steps;
   return LBM_OK;
 }
