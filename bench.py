@@ -62,11 +62,11 @@ def profile_figures():
     return out
 
 
-def sweep_instances(prec):
+def sweep_instances(prec, world_size=1, rank=0):
     from paper_1410_2569_gb300 import default_params, inputs
     solid = inputs.flat_walls(NX, NY)
     out = []
-    for c in inputs.sweep_cases():
+    for c in inputs.sweep_cases(world_size, rank):
         p = default_params(prec=prec, tau_nu_L=c["tau_nu_L"], tau_nu_V=c["tau_nu_V"])
         out.append(dict(nx=NX, ny=NY, params=p, solid=solid, fsi=c["fsi"], gw=c["gw"]))
     return out
@@ -156,6 +156,16 @@ def droplet_density(nx, ny, x0, y0, R, W, rho_L=500.0, rho_V=1.0):
     return rho_V + 0.5 * (rho_L - rho_V) * (1.0 - np.tanh(2.0 * (r - R) / W))
 
 
+def max_over_ranks(value, dist=None, device="cpu"):
+    """The largest value over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_device(lat, stream, steps, warmup):
     import torch
     lat.step(warmup)
@@ -187,7 +197,7 @@ def run_ours(args, ws, rank, local):
     y_w = inputs.wall_height("copy")
     precs = ("fp32", "fp64") if args.prec == "both" else (args.prec,)
     for prec in precs:
-        insts = sweep_instances(prec)
+        insts = sweep_instances(prec, ws, rank)
         lat = lbm.Lattice(insts, stream=stream)
         for k in range(len(insts)):
             lat.init_droplet(NX / 2, y_w, R, inputs.SWEEP_WIDTH, inst=k)
@@ -205,10 +215,7 @@ def run_ours(args, ws, rank, local):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        t = torch.tensor([dt], device="cuda")
-        if dist:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+        dt = max_over_ranks(dt, dist, "cuda")
         mlups = ws * nodes * args.steps / dt / 1e6
         # contact angle of one tracked instance after warm-up + timed steps
         d = lat.diagnostics(inst=11, y_w=y_w, x_ref=NX / 2)

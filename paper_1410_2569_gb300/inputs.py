@@ -55,16 +55,18 @@ GW_RANGES = {"density": (-0.14, 0.28), "psi": (-1.5, 2.25), "modified": (-0.2, 0
 SWEEP_WIDTH = 4.0
 
 
-def sweep_cases():
+def sweep_cases(world_size=1, rank=0):
     """72 cases of the paper-shaped sweep: each interaction at 12 G_w values
     spread uniformly over the ranges of Sec. III.C (GW_RANGES), times
     vapour/liquid kinematic-viscosity ratios 1 and 10 with nu_L = 1/30
-    (tau_nu,L = 0.6)."""
+    (tau_nu,L = 0.6).  With world_size > 1 the G_w grid is world_size times
+    finer and rank r takes every world_size-th value from offset r: 72
+    distinct cases per rank, the union over ranks covering the finer sweep."""
     ranges = GW_RANGES
     cases = []
     for ratio in (1.0, 10.0):
         for fsi, (lo, hi) in ranges.items():
-            for gw in np.linspace(lo, hi, 12):
+            for gw in np.linspace(lo, hi, 12 * world_size)[rank::world_size]:
                 nu_L = 1.0 / 30.0
                 cases.append(dict(fsi=fsi, gw=float(gw), tau_nu_L=0.5 + 3.0 * nu_L,
                                   tau_nu_V=0.5 + 3.0 * nu_L * ratio, ratio=ratio))
