@@ -221,6 +221,26 @@ def run_ours(args, ws, rank, local):
         d = lat.diagnostics(inst=11, y_w=y_w, x_ref=NX / 2)
         results[prec] = dict(dt=dt, mlups=mlups, clocks=clk.summary(), theta=d["theta_deg"],
                              lat=lat)
+    # the large single lattice (8192 x 4096, striped wall, 2000 droplets):
+    # an extra figure beside the sweep, one lattice far larger than L2
+    large = None
+    if args.large and args.prec == "both":
+        large = {}
+        lnx, lny = 8192, 4096
+        solid_l, gw_l, drops_l = inputs.large_striped(lnx, lny, 2000, seed=0)
+        rho_l = inputs.droplet_field(lnx, lny, drops_l, 4.0)
+        for prec, nsteps in (("fp32", 50), ("fp64", 10)):
+            lat = lbm.Lattice.single(lnx, lny, lbm.default_params(prec=prec), solid_l, "modified",
+                                     gw_l, stream=stream)
+            lat.set_density(rho_l)
+            lat.step(3)
+            lat.sync()
+            dt_l = max_over_ranks(time_device(lat, stream, nsteps, 0), dist, "cuda")
+            ml = ws * lnx * lny * nsteps / dt_l / 1e6
+            large[prec] = {"value": round(ml, 1), "unit": "MLUPS", "steps": nsteps,
+                           "ms_per_step": round(dt_l / nsteps * 1e3, 4),
+                           "algorithmic_GBps": round(ml * 1e6 * BYTES_PER_NODE[prec] / 1e9 / ws, 1)}
+            lat.close()
     # end-to-end through the C ABI with host buffers: host density fields in,
     # `chunk` steps, host rho/ux/uy fields out, per e2e iteration
     e2e = None
@@ -305,6 +325,10 @@ def run_ours(args, ws, rank, local):
                  "clocks": f64["clocks"]},
         "theta_fp32_vs_fp64_deg": round(abs(f32["theta"] - f64["theta"]), 6),
         "e2e": e2e,
+        "large_lattice": None if large is None else dict(
+            large, workload="8192x4096, bottom wall in 64-node G_w stripes -0.1/0.3, "
+                            "2000 droplets R 10-40, modified interaction",
+            hbm_frac_fp32=round(large["fp32"]["algorithmic_GBps"] / hbm, 4)),
         "gpu_launches": args.steps,
         "clocks": f32["clocks"],
         "cpu_baseline": cpu,
@@ -379,6 +403,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-large", dest="large", action="store_false",
+                    help="skip the extra 8192x4096 single-lattice figure")
     ap.add_argument("--prec", default="both", choices=["both", "fp32", "fp64"],
                     help="a single precision prints only its timings (profiling runs)")
     args = ap.parse_args()

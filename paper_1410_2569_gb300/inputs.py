@@ -120,3 +120,60 @@ def place_droplets(nx, ny, count, rmin, rmax, seed=0, gap=4.0, y_floor=1.0, max_
         if ok:
             placed.append((x0, y_floor, R))
     return placed
+
+
+def place_droplets_2d(nx, ny, count, rmin, rmax, seed=0, gap=8.0, y_min=1.0, y_max=None,
+                      max_tries=400000):
+    """Non-overlapping circles (x0, y0, R), R uniform in [rmin, rmax], centres
+    uniform in [0, nx) x [y_min, y_max] (periodic in x), at least `gap` apart;
+    rejection-sampled from a seed.  Returns as many as fit."""
+    rng = np.random.default_rng(seed)
+    y_max = ny - 1 - rmax - 4 if y_max is None else y_max
+    xs, ys, rs = np.zeros(count), np.zeros(count), np.zeros(count)
+    n, tries = 0, 0
+    while n < count and tries < max_tries:
+        tries += 1
+        R = float(rng.uniform(rmin, rmax))
+        x0 = float(rng.uniform(0, nx))
+        y0 = float(rng.uniform(y_min, y_max))
+        if n:
+            dx = np.abs(xs[:n] - x0)
+            dx = np.minimum(dx, nx - dx)
+            if np.any(np.hypot(dx, ys[:n] - y0) < rs[:n] + R + gap):
+                continue
+        xs[n], ys[n], rs[n] = x0, y0, R
+        n += 1
+    return list(zip(xs[:n], ys[:n], rs[:n]))
+
+
+def droplet_field(nx, ny, drops, width, rho_L=500.0, rho_V=1.0):
+    """Initial density field of several droplets: for each node the largest
+    of the single-droplet tanh profiles rho_V + (rho_L - rho_V)/2 *
+    (1 - tanh(2 (r - R) / width)), r the distance with the minimum image in x.
+    Built tile by tile around each droplet."""
+    rho = np.full((ny, nx), float(rho_V))
+    reach = 4.0 * width
+    for (x0, y0, R) in drops:
+        ylo, yhi = max(0, int(y0 - R - reach)), min(ny, int(y0 + R + reach) + 2)
+        span = int(R + reach) + 2
+        cols = (np.arange(int(x0) - span, int(x0) + span + 1)) % nx
+        yy = np.arange(ylo, yhi)[:, None].astype(np.float64)
+        dx = (cols[None, :].astype(np.float64) - x0)
+        dx -= nx * np.floor(dx / nx + 0.5)
+        r = np.sqrt(dx * dx + (yy - y0) ** 2)
+        prof = rho_V + 0.5 * (rho_L - rho_V) * (1.0 - np.tanh(2.0 * (r - R) / width))
+        sub = rho[ylo:yhi][:, cols]
+        rho[ylo:yhi, cols] = np.maximum(sub, prof)
+    return rho
+
+
+def large_striped(nx=8192, ny=4096, count=2000, seed=0):
+    """The large workload: flat walls, the bottom wall patterned in 64-node
+    stripes of G_w = -0.1 and 0.3 (about 69 and 143 deg for the modified
+    interaction, Fig. 4), `count` droplets of radius 10..40 placed without
+    overlap.  Returns (solid, gw field, droplets)."""
+    solid = flat_walls(nx, ny)
+    gw = stripes(nx, ny, solid, 64, -0.1, 0.3)
+    gw[ny - 1, :] = 0.0  # neutral top wall
+    drops = place_droplets_2d(nx, ny, count, 10.0, 40.0, seed=seed, gap=8.0, y_min=1.0)
+    return solid, gw, drops
