@@ -239,6 +239,21 @@ static void fill_consts(Consts<T>& K, const lbm_params& p, double rho_ref) {
   K.tau_hi = (T)std::max(p.tau_nu_L, p.tau_nu_V);
   K.rho_V = (T)p.rho_V;
   K.rho_ref = (T)rho_ref;
+  const double h_e = 1.0 - 0.5 * s_e, h_z = 1.0 - 0.5 * s_z, h_q = 1.0 - 0.5 * s_q;
+  const double c_e = h_e * 12.0 * p.sigma * G2 / (p.tau_e - 0.5);
+  const double c_z = h_z * 12.0 * p.sigma * G2 / (p.tau_zeta - 0.5);
+  const double s_nu = 1.0 / p.tau_nu_L, h_nu = 1.0 - 0.5 * s_nu;
+  K.ke_v = (T)(h_e / 6.0);
+  K.ke_g = (T)(c_e / 36.0);
+  K.ke_n = (T)(s_e / 36.0);
+  K.kz_v = (T)(h_z / 6.0);
+  K.kz_g = (T)(c_z / 36.0);
+  K.kz_n = (T)(s_z / 36.0);
+  K.kq = (T)(s_q / 12.0);
+  K.kq_F = (T)(h_q / 12.0);
+  K.knu = (T)(s_nu / 4.0);
+  K.hnu2 = (T)(h_nu / 2.0);
+  K.hnu4 = (T)(h_nu / 4.0);
 }
 
 static void fill_desc(Inst& I, int prec, int* d_err) {
@@ -403,7 +418,8 @@ static lbm_status make_inst(const lbm_instance_desc& d, Inst& I) {
   lbm_status st = validate_params(d.params);
   if (st != LBM_OK) return st;
   if (d.nx < 3 || d.ny < 4) return fail(LBM_ERR_ARG, "lattice must be at least 3 x 4 (got %d x %d)", d.nx, d.ny);
-  if ((long long)d.nx * d.ny * Q >= (1LL << 40)) return fail(LBM_ERR_ARG, "lattice too large");
+  if ((long long)d.nx * d.ny * Q >= (1LL << 31))
+    return fail(LBM_ERR_ARG, "lattice too large: 9 * nx * ny must stay below 2^31");
   if ((int)d.fsi < 0 || (int)d.fsi > 2) return fail(LBM_ERR_ARG, "unknown interaction %d", (int)d.fsi);
   I.nx = d.nx;
   I.ny = d.ny;

@@ -42,6 +42,10 @@ struct Consts {
   T tauV, dtau, tau_lo, tau_hi;  // tau_nu(rho) = tauV + (rho - rho_V) dtau
   T rho_V;
   T rho_ref;           // storage shift (0 in FP64)
+  // the relaxation of Eq. (4) with the diagonal of M^-1 folded in:
+  // E = ke_v vF + ke_g g2 - ke_n ne, P = -(kz_v vF + kz_g g2 + kz_n nz),
+  // QX = -kq (qx + mx) - kq_F Fx, XX = hnu2 (..) - knu (..), XY = hnu4 (..) - knu (..)
+  T ke_v, ke_g, ke_n, kz_v, kz_g, kz_n, kq, kq_F, knu, hnu2, hnu4;
 };
 
 struct __align__(16) InstDesc {
