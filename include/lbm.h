@@ -229,11 +229,13 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, long T, double theta_target, double y_w, do
    the one persistent launch) in a CUDA graph, reused for every later call
    with the same n.  stages selects the step pipeline: 1 = blocks marching up
    rows with loads prefetched into registers; 2 = independent warps, each
-   marching up a 30-column strip (no block barriers; persistent is ignored);
-   8 or 16 = blocks marching up rows with a TMA ring of that many source rows
+   marching up a 30-column strip (no block barriers; persistent is ignored),
+   with FP32 storage two rows at a time on the paired FP32 instructions;
+   3 = the same warp strips one row at a time; 8 or 16 = blocks marching up rows with a TMA ring of that many source rows
    in shared memory (FP32 storage, every lattice width a multiple of 4);
-   0 = automatic (warp strips).  Results do not depend on any of these
-   choices. */
+   0 = automatic (warp strips, as 2).  Results do not depend on any of these
+   choices.  A persistent launch needs one parameter set across the batch
+   (LBM_ERR_ARG otherwise). */
 lbm_status lbm_set_launch(lbm_ctx* ctx, int bx, int h, int persistent, int graph, int stages);
 
 /* Writes the state of every lattice (post-collision populations, wall

@@ -56,15 +56,15 @@ __device__ __forceinline__ long long nb(const InstDesc& I, const Node& n, int dx
 // psi^2 = a rho + b (Eq. 15); returns a for d(psi^2)/d(rho)
 __device__ __forceinline__ double psi2_and_slope(const InstDesc& I, double rho, double& a) {
   double b;
-  if (rho <= I.rho1) {
-    a = I.aV;
+  if (rho <= I.ph.rho1) {
+    a = I.ph.aV;
     b = 0.0;
-  } else if (rho <= I.rho2) {
-    a = I.aM;
-    b = I.bM;
+  } else if (rho <= I.ph.rho2) {
+    a = I.ph.aM;
+    b = I.ph.bM;
   } else {
-    a = I.aL;
-    b = I.bL;
+    a = I.ph.aL;
+    b = I.ph.bL;
   }
   return a * rho + b;
 }
@@ -95,8 +95,8 @@ __global__ void k_adj_fields(const InstDesc* __restrict__ insts, const double* _
 }
 
 __device__ __forceinline__ int ghost_offset(const InstDesc& I, uint16_t fl) {
-  if (I.ghost != LBM_GHOST_COPY && I.ghost != LBM_GHOST_MIRROR) return 0;
-  const int d = I.ghost == LBM_GHOST_COPY ? 1 : 2;
+  if (I.ph.ghost != LBM_GHOST_COPY && I.ph.ghost != LBM_GHOST_MIRROR) return 0;
+  const int d = I.ph.ghost == LBM_GHOST_COPY ? 1 : 2;
   if (fl & NF_GHOST_UP) return d;
   if (fl & NF_GHOST_DOWN) return -d;
   return 0;
@@ -123,7 +123,7 @@ __global__ void k_adj_walls(const InstDesc* __restrict__ insts, const double* __
   for (int a = 0; a < Q; ++a) l[a] = lam[a * N + n.i];
   const uint16_t fl = I.flags[n.i];
   double Fx = 0.0, Fy = 0.0;
-  if (I.wall == LBM_WALL_NEQ_ONNODE && (fl & NF_NEQ_BOTTOM)) {
+  if (I.ph.wall == LBM_WALL_NEQ_ONNODE && (fl & NF_NEQ_BOTTOM)) {
     // f2 = f4', f5 = f7' - (f1' - f3')/2 - (Fx + Fy)/4, f6 = f8' + (f1' - f3')/2 + (Fx - Fy)/4
     const double l2 = l[2], l5 = l[5], l6 = l[6];
     l[1] += -0.5 * l5 + 0.5 * l6;
@@ -134,7 +134,7 @@ __global__ void k_adj_walls(const InstDesc* __restrict__ insts, const double* __
     Fx = -0.25 * l5 + 0.25 * l6;
     Fy = -0.25 * l5 - 0.25 * l6;
     l[2] = l[5] = l[6] = 0.0;
-  } else if (I.wall == LBM_WALL_NEQ_ONNODE && (fl & NF_NEQ_TOP)) {
+  } else if (I.ph.wall == LBM_WALL_NEQ_ONNODE && (fl & NF_NEQ_TOP)) {
     // f4 = f2', f8 = f6' - (f1' - f3')/2 - (Fx - Fy)/4, f7 = f5' + (f1' - f3')/2 + (Fx + Fy)/4
     const double l4 = l[4], l8 = l[8], l7 = l[7];
     l[1] += -0.5 * l8 + 0.5 * l7;
@@ -163,7 +163,7 @@ __global__ void k_adj_node(const InstDesc* __restrict__ insts, const double* __r
   const long long N = I.plane;
   const uint16_t fl = I.flags[n.i];
   if (fl & NF_SELF_SOLID) return;
-  const Consts<double>& K = I.cd;
+  const Consts<double>& K = I.ph.cd;
   // forward quantities at x
   double fx[Q];
   for (int a = 0; a < Q; ++a) fx[a] = f[a * N + n.i];
@@ -174,7 +174,7 @@ __global__ void k_adj_node(const InstDesc* __restrict__ insts, const double* __r
     gx += wgt(a) * pn * EX[a];
     gy += wgt(a) * pn * EY[a];
   }
-  const bool skip = I.ghost == LBM_GHOST_SKIP && (fl & NF_SRC_SOLID);
+  const bool skip = I.ph.ghost == LBM_GHOST_SKIP && (fl & NF_SRC_SOLID);
   const double G = K.G;
   double Fx = skip ? 0.0 : -G * p * gx, Fy = skip ? 0.0 : -G * p * gy;
   const double2 A = I.A[n.i];
@@ -187,7 +187,7 @@ __global__ void k_adj_node(const InstDesc* __restrict__ insts, const double* __r
   for (int a = 0; a < Q; ++a) {
     const long long j = nb(I, n, EX[a], EY[a]);
     if (!(I.flags[j] & NF_SELF_SOLID)) ls[a] = lamp[a * N + j];
-    else ls[a] = I.wall == LBM_WALL_HALFWAY_BB ? lam[OPP[a] * N + n.i] : 0.0;
+    else ls[a] = I.ph.wall == LBM_WALL_HALFWAY_BB ? lam[OPP[a] * N + n.i] : 0.0;
   }
   // moment-space adjoint: lam_dm = D^-1 M lam*
   const double a13 = ls[1] + ls[3], a24 = ls[2] + ls[4], a57 = ls[5] + ls[7], a68 = ls[6] + ls[8];
@@ -317,7 +317,7 @@ __global__ void k_adj_gather(const InstDesc* __restrict__ insts, const double* _
   if (fl & NF_SELF_SOLID) {
     for (int a = 0; a < Q; ++a) lam_out[a * N + n.i] = 0.0;
     // dL/dG_w(z): A(x) = sum_a omega_a G_w(x + e_a) s(x + e_a) e_a
-    const double scale = I.omega_cs2w ? 1.0 / 3.0 : 1.0;
+    const double scale = I.ph.omega_cs2w ? 1.0 / 3.0 : 1.0;
     double g = 0.0;
     for (int a = 1; a < Q; ++a) {
       const long long j = nb(I, n, -EX[a], -EY[a]);
@@ -330,8 +330,8 @@ __global__ void k_adj_gather(const InstDesc* __restrict__ insts, const double* _
   }
   double lpsi = lam_psi_loc[n.i] + stencil_adjoint(I, n, lam_g);
   // this node may be the ghost source of a solid node s (psi(s) = psi(z))
-  if (I.ghost == LBM_GHOST_COPY || I.ghost == LBM_GHOST_MIRROR) {
-    const int d = I.ghost == LBM_GHOST_COPY ? 1 : 2;
+  if (I.ph.ghost == LBM_GHOST_COPY || I.ph.ghost == LBM_GHOST_MIRROR) {
+    const int d = I.ph.ghost == LBM_GHOST_COPY ? 1 : 2;
     for (int sgn = -1; sgn <= 1; sgn += 2) {
       Node s;
       s.x = n.x;

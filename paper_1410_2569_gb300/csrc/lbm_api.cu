@@ -77,6 +77,11 @@ struct lbm_ctx {
   InstDesc* d_desc = nullptr;
   WorkItem* d_items = nullptr;
   int n_items = 0;
+  // parameter classes: instances whose PhysDesc agree byte for byte; the
+  // items of class j are [cls_beg[j], cls_beg[j] + cls_n[j]) and go out in
+  // one launch with cls[j] as its kernel parameter
+  std::vector<PhysDesc> cls;
+  std::vector<int> cls_beg, cls_n;
   int* d_err = nullptr;       // [0] latched error bits
   unsigned* d_barrier = nullptr;  // [0] arrival counter, [1] error word of the persistent kernel
   int parity = 0;
@@ -233,16 +238,10 @@ static void fill_consts(Consts<T>& K, const lbm_params& p, double rho_ref) {
   K.c_z = (T)((1.0 - 0.5 * s_z) * 12.0 * p.sigma * G2 / (p.tau_zeta - 0.5));
   K.s_nu = (T)(1.0 / p.tau_nu_L);
   K.h_nu = (T)(1.0 - 0.5 / p.tau_nu_L);
-  K.tauV = (T)p.tau_nu_V;
-  K.dtau = (T)((p.tau_nu_L - p.tau_nu_V) / (p.rho_L - p.rho_V));
-  K.tau_lo = (T)std::min(p.tau_nu_L, p.tau_nu_V);
-  K.tau_hi = (T)std::max(p.tau_nu_L, p.tau_nu_V);
-  K.rho_V = (T)p.rho_V;
   K.rho_ref = (T)rho_ref;
   const double h_e = 1.0 - 0.5 * s_e, h_z = 1.0 - 0.5 * s_z, h_q = 1.0 - 0.5 * s_q;
   const double c_e = h_e * 12.0 * p.sigma * G2 / (p.tau_e - 0.5);
   const double c_z = h_z * 12.0 * p.sigma * G2 / (p.tau_zeta - 0.5);
-  const double s_nu = 1.0 / p.tau_nu_L, h_nu = 1.0 - 0.5 * s_nu;
   K.ke_v = (T)(h_e / 6.0);
   K.ke_g = (T)(c_e / 36.0);
   K.ke_n = (T)(s_e / 36.0);
@@ -251,21 +250,42 @@ static void fill_consts(Consts<T>& K, const lbm_params& p, double rho_ref) {
   K.kz_n = (T)(s_z / 36.0);
   K.kq = (T)(s_q / 12.0);
   K.kq_F = (T)(h_q / 12.0);
-  K.knu = (T)(s_nu / 4.0);
-  K.hnu2 = (T)(h_nu / 2.0);
-  K.hnu4 = (T)(h_nu / 4.0);
+}
+
+template <typename T>
+static void fill_visc(Visc<T>& V, const lbm_params& p) {
+  const double s_nu = 1.0 / p.tau_nu_L, h_nu = 1.0 - 0.5 * s_nu;
+  V.knu = (T)(s_nu / 4.0);
+  V.hnu2 = (T)(h_nu / 2.0);
+  V.hnu4 = (T)(h_nu / 4.0);
+  V.tauV = (T)p.tau_nu_V;
+  V.dtau = (T)((p.tau_nu_L - p.tau_nu_V) / (p.rho_L - p.rho_V));
+  V.tau_lo = (T)std::min(p.tau_nu_L, p.tau_nu_V);
+  V.tau_hi = (T)std::max(p.tau_nu_L, p.tau_nu_V);
+  V.rho_V = (T)p.rho_V;
+}
+
+// The part of PhysDesc that the step kernels read: the viscosity (s_nu,
+// h_nu) is per instance (Visc in the descriptor head), so instances that
+// differ only in viscosity share a launch.
+static PhysDesc class_key(PhysDesc ph) {
+  ph.cd.s_nu = ph.cd.h_nu = 0.0;
+  ph.cf.s_nu = ph.cf.h_nu = 0.f;
+  return ph;
 }
 
 static void fill_desc(Inst& I, int prec, int* d_err) {
   InstDesc& d = I.desc;
+  PhysDesc& ph = d.ph;
   const lbm_params& p = I.p;
+  memset(&ph, 0, sizeof ph);  // padding too: classes compare the bytes
   d.nx = I.nx;
   d.ny = I.ny;
   d.fsi = (int)I.fsi;
-  d.wall = (int)p.wall;
-  d.ghost = (int)p.ghost;
+  ph.wall = (int)p.wall;
+  ph.ghost = (int)p.ghost;
   d.var_nu = p.tau_nu_L != p.tau_nu_V;
-  d.omega_cs2w = p.omega == LBM_OMEGA_CS2W;
+  ph.omega_cs2w = p.omega == LBM_OMEGA_CS2W;
   d.plane = (long long)I.nx * I.ny;
   d.f[0] = I.f[0];
   d.f[1] = I.f[1];
@@ -279,28 +299,30 @@ static void fill_desc(Inst& I, int prec, int* d_err) {
   const double cs2 = 1.0 / 3.0, kV = p.eos_p[0], kM = p.eos_p[1], kL = p.eos_p[2];
   const double r1 = p.eos_p[3], r2 = p.eos_p[4];
   const double g = 2.0 * cs2 / (-p.G);
-  d.rho1 = r1;
-  d.rho2 = r2;
-  d.aV = g * (1.0 - kV);
-  d.aM = g * (1.0 - kM);
-  d.bM = -g * (kV - kM) * r1;
-  d.aL = g * (1.0 - kL);
-  d.bL = -g * (kV * r1 + kM * (r2 - r1) - kL * r2);
+  ph.rho1 = r1;
+  ph.rho2 = r2;
+  ph.aV = g * (1.0 - kV);
+  ph.aM = g * (1.0 - kM);
+  ph.bM = -g * (kV - kM) * r1;
+  ph.aL = g * (1.0 - kL);
+  ph.bL = -g * (kV * r1 + kM * (r2 - r1) - kL * r2);
   auto split = [](double v, float& hi, float& lo) {
     hi = (float)v;
     lo = (float)(v - (double)hi);
   };
-  const double ab[3][2] = {{d.aV, 0.0}, {d.aM, d.bM}, {d.aL, d.bL}};
+  const double ab[3][2] = {{ph.aV, 0.0}, {ph.aM, ph.bM}, {ph.aL, ph.bL}};
   for (int b = 0; b < 3; ++b) {
-    split(ab[b][0], d.eosf[b][0], d.eosf[b][1]);
-    split(ab[b][1], d.eosf[b][2], d.eosf[b][3]);
+    split(ab[b][0], ph.eosf[b][0], ph.eosf[b][1]);
+    split(ab[b][1], ph.eosf[b][2], ph.eosf[b][3]);
   }
-  split(r1, d.thrf[0], d.thrf[1]);
-  split(r2, d.thrf[2], d.thrf[3]);
+  split(r1, ph.thrf[0], ph.thrf[1]);
+  split(r2, ph.thrf[2], ph.thrf[3]);
   // the FP32 storage shift is rounded to FP32 so that it is exact in both precisions
   const double rho_ref = prec == LBM_FP64 ? 0.0 : (double)(float)p.rho_ref;
-  fill_consts<double>(d.cd, p, rho_ref);
-  fill_consts<float>(d.cf, p, rho_ref);
+  fill_consts<double>(ph.cd, p, rho_ref);
+  fill_consts<float>(ph.cf, p, rho_ref);
+  fill_visc<double>(d.vd, p);
+  fill_visc<float>(d.vf, p);
 }
 
 static void free_inst(Inst& I) {
@@ -358,7 +380,9 @@ static lbm_status upload_inst(lbm_ctx* c, Inst& I) {
 static lbm_status build_items(lbm_ctx* c) {
   // block rows: a block of bx threads covers bx - 2 columns (its two edge
   // lanes evaluate the halo columns); warp strips: each warp covers 30
-  const bool warp_mode = c->stages == 2 || c->stages == 0;
+  const bool warp_mode = c->stages == 0 || c->stages == 2 || c->stages == 3;
+  // FP32 storage in warp strips: two rows per lane unless one is asked for
+  const bool two_rows = warp_mode && c->stages != 3 && c->prec == LBM_FP32_SHIFTED;
   int bx = c->bx;
   if (bx <= 0) {
     // widest instance decides; whole rows up to 512 threads, else 256-wide strips
@@ -367,11 +391,30 @@ static lbm_status build_items(lbm_ctx* c) {
     if (maxnx + 2 <= 512) bx = ((maxnx + 2 + 31) / 32) * 32;
     else bx = 256;
   }
-  if (warp_mode && c->bx <= 0) bx = 256;
+  // warp strips: 8 warps per block; 4 for two rows per lane (about 150
+  // registers a thread: three such blocks fit an SM, two of 8 warps would not)
+  if (warp_mode && c->bx <= 0) bx = two_rows ? 128 : 256;
   bx = std::max(32, std::min(warp_mode ? 256 : 512, ((bx + 31) / 32) * 32));
   const int cols = warp_mode ? 30 : bx - 2;
-  std::vector<WorkItem> items;
-  for (int k = 0; k < (int)c->inst.size(); ++k) {
+  // parameter classes, in order of first appearance
+  c->cls.clear();
+  c->cls_beg.clear();
+  c->cls_n.clear();
+  std::vector<int> inst_cls(c->inst.size());
+  for (size_t k = 0; k < c->inst.size(); ++k) {
+    const PhysDesc ph = class_key(c->inst[k].desc.ph);
+    size_t j = 0;
+    while (j < c->cls.size() && memcmp(&c->cls[j], &ph, sizeof ph) != 0) ++j;
+    if (j == c->cls.size()) c->cls.push_back(ph);
+    inst_cls[k] = (int)j;
+  }
+  if (c->persistent && c->cls.size() > 1) {
+    c->persistent = 0;
+    return fail(LBM_ERR_ARG, "a persistent launch needs one parameter set across the batch "
+                             "(this batch has %d)", (int)c->cls.size());
+  }
+  // items of instance k: h-row segments of cols-wide strips
+  auto add_items = [&](int k, std::vector<WorkItem>& items) {
     const Inst& I = c->inst[k];
     int h = c->h;
     if (h <= 0) {
@@ -380,9 +423,17 @@ static lbm_status build_items(lbm_ctx* c) {
       const int hmax = warp_mode ? 32 : 64;
       const int nseg = (I.ny + hmax - 1) / hmax;
       h = (I.ny + nseg - 1) / nseg;
+      if (two_rows) h += h & 1;  // whole row pairs
     }
     for (int y0 = 0; y0 < I.ny; y0 += h)
       for (int x0 = 0; x0 < I.nx; x0 += cols) items.push_back({k, x0, y0, std::min(I.ny, y0 + h)});
+  };
+  std::vector<WorkItem> items;
+  for (int j = 0; j < (int)c->cls.size(); ++j) {
+    c->cls_beg.push_back((int)items.size());
+    for (int k = 0; k < (int)c->inst.size(); ++k)
+      if (inst_cls[k] == j) add_items(k, items);
+    c->cls_n.push_back((int)items.size() - c->cls_beg[j]);
   }
   cudaFree(c->d_items);
   c->d_items = nullptr;
@@ -400,7 +451,8 @@ static lbm_status build_items(lbm_ctx* c) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   while (S >= 8 && tma_smem_bytes(bx, S) > (size_t)optin) S /= 2;
-  c->stages_used = warp_mode ? PIPE_WARP : ((tma_ok && c->stages != 1 && S >= 8) ? S : 0);
+  c->stages_used = warp_mode ? (c->stages == 3 ? PIPE_WARP1 : PIPE_WARP)
+                              : ((tma_ok && c->stages != 1 && S >= 8) ? S : 0);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   c->graphs.clear();
   return LBM_OK;
@@ -582,19 +634,27 @@ extern "C" lbm_status lbm_init_droplet(lbm_ctx* c, int inst, double x0, double y
   return lbm_set_density(c, inst, rho.data(), 0);
 }
 
+// one time step: one launch per parameter class
+static cudaError_t launch_one_step(lbm_ctx* c, int parity, cudaStream_t s) {
+  for (size_t j = 0; j < c->cls.size(); ++j) {
+    cudaError_t e = launch_step(c->prec, c->cls[j], c->d_desc, c->d_items + c->cls_beg[j],
+                                c->cls_n[j], parity, c->bx_used, c->stages_used, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 static lbm_status enqueue_steps(lbm_ctx* c, long n) {
-  if (c->persistent && c->stages_used != PIPE_WARP) {
-    // one cooperative launch for all n steps; the kernel's error word is
-    // separate from the context's so that a time-out does not hide behind a
-    // stale value
+  if (c->persistent && !is_warp_pipe(c->stages_used)) {
+    // one cooperative launch for all n steps (one parameter class, checked
+    // when the items are built); the kernel's error word is separate from
+    // the context's so that a time-out does not hide behind a stale value
     CK(cudaMemsetAsync(c->d_barrier + 1, 0, sizeof(unsigned), c->stream));
-    CK(launch_step_persistent(c->prec, c->d_desc, c->d_items, c->n_items, c->parity, n,
-                              c->bx_used, c->stages_used, c->d_barrier, c->stream));
+    CK(launch_step_persistent(c->prec, c->cls[0], c->d_desc, c->d_items, c->n_items, c->parity,
+                              n, c->bx_used, c->stages_used, c->d_barrier, c->stream));
     return LBM_OK;
   }
-  for (long k = 0; k < n; ++k)
-    CK(launch_step(c->prec, c->d_desc, c->d_items, c->n_items, (int)((c->parity + k) & 1),
-                   c->bx_used, c->stages_used, c->stream));
+  for (long k = 0; k < n; ++k) CK(launch_one_step(c, (int)((c->parity + k) & 1), c->stream));
   return LBM_OK;
 }
 
@@ -611,16 +671,16 @@ extern "C" lbm_status lbm_step(lbm_ctx* c, long n) {
       cudaGraph_t g;
       cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        if (c->persistent && c->stages_used != PIPE_WARP) {
+        if (c->persistent && !is_warp_pipe(c->stages_used)) {
           // one persistent launch for all n steps, captured once
           e = cudaMemsetAsync(c->d_barrier + 1, 0, sizeof(unsigned), cap);
           if (e == cudaSuccess)
-            e = launch_step_persistent(c->prec, c->d_desc, c->d_items, c->n_items, c->parity, n,
-                                       c->bx_used, c->stages_used, c->d_barrier, cap);
+            e = launch_step_persistent(c->prec, c->cls[0], c->d_desc, c->d_items, c->n_items,
+                                       c->parity, n, c->bx_used, c->stages_used, c->d_barrier,
+                                       cap);
         } else {
           for (long k = 0; k < n && e == cudaSuccess; ++k)
-            e = launch_step(c->prec, c->d_desc, c->d_items, c->n_items,
-                            (int)((c->parity + k) & 1), c->bx_used, c->stages_used, cap);
+            e = launch_one_step(c, (int)((c->parity + k) & 1), cap);
         }
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e == cudaSuccess) e = e2;
@@ -722,8 +782,9 @@ extern "C" lbm_status lbm_set_launch(lbm_ctx* c, int bx, int h, int persistent, 
                                       int stages) {
   if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
   if (bx < 0 || bx > 512 || h < 0) return fail(LBM_ERR_ARG, "need 0 <= bx <= 512 and h >= 0");
-  if (!(stages == 0 || stages == 1 || stages == 2 || stages == 8 || stages == 16))
+  if (!(stages >= 0 && stages <= 3) && stages != 8 && stages != 16)
     return fail(LBM_ERR_ARG, "stages must be 0 (automatic), 1 (block rows), 2 (warp strips), "
+                             "3 (warp strips, one row per lane), "
                              "8 or 16 (TMA ring)");
   CK(cudaStreamSynchronize(c->stream));
   c->bx = bx;
@@ -1162,9 +1223,12 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, int steps, int* bx_out, int* h_ou
   struct Cand {
     int bx, h, stages;
   };
-  std::vector<Cand> cands = {{256, 16, 2}, {256, 25, 2}, {256, 32, 2}, {256, 48, 2},
-                             {128, 25, 2}, {128, 32, 2}, {224, 32, 1}, {224, 50, 1},
-                             {416, 50, 1}, {224, 50, 8}, {416, 50, 8}};
+  // warp strips (two rows per lane with FP32 storage: even h), warp strips
+  // one row per lane, block rows, TMA block rows
+  std::vector<Cand> cands = {{128, 16, 2}, {128, 24, 2}, {128, 32, 2}, {64, 32, 2},
+                             {256, 32, 2}, {256, 25, 3}, {256, 32, 3}, {128, 32, 3},
+                             {224, 32, 1}, {224, 50, 1}, {416, 50, 1}, {224, 50, 8},
+                             {416, 50, 8}};
   const int saved[5] = {c->bx, c->h, c->persistent, c->use_graph, c->stages};
   c->persistent = 0;
   c->use_graph = 0;

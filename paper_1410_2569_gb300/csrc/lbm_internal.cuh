@@ -14,6 +14,7 @@
 //             Sec. III.A when the next step pulls into a wall node.
 #pragma once
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "lbm.h"
@@ -38,28 +39,33 @@ struct Consts {
   T s_e, s_z, s_q;     // 1/tau_e, 1/tau_zeta, 1/tau_q of Eq. (2)
   T h_e, h_z, h_q;     // 1 - s/2
   T c_e, c_z;          // (1 - s/2) * 12 sigma G^2 / (tau - 1/2), Eq. (9)
-  T s_nu, h_nu;        // constant-viscosity rate and 1 - s_nu/2
-  T tauV, dtau, tau_lo, tau_hi;  // tau_nu(rho) = tauV + (rho - rho_V) dtau
-  T rho_V;
+  T s_nu, h_nu;        // constant-viscosity rate and 1 - s_nu/2 (adjoint)
   T rho_ref;           // storage shift (0 in FP64)
   // the relaxation of Eq. (4) with the diagonal of M^-1 folded in:
   // E = ke_v vF + ke_g g2 - ke_n ne, P = -(kz_v vF + kz_g g2 + kz_n nz),
-  // QX = -kq (qx + mx) - kq_F Fx, XX = hnu2 (..) - knu (..), XY = hnu4 (..) - knu (..)
-  T ke_v, ke_g, ke_n, kz_v, kz_g, kz_n, kq, kq_F, knu, hnu2, hnu4;
+  // QX = -kq (qx + mx) - kq_F Fx (the shear rates are in Visc)
+  T ke_v, ke_g, ke_n, kz_v, kz_g, kz_n, kq, kq_F;
 };
 
-struct __align__(16) InstDesc {
-  int nx, ny;
-  int fsi, wall, ghost, var_nu;
-  int omega_cs2w;   // omega_alpha = cs^2 w_alpha (else w_alpha) in A(x)
+// Shear viscosity of one instance: XX = hnu2 (..) - knu (..), XY = hnu4 (..)
+// - knu (..) with knu = s_nu / 4, hnu2 = (1 - s_nu / 2) / 2, hnu4 = hnu2 / 2
+// (the diagonal of M^-1 folded in), s_nu = 1 / tau_nu_L; or, with a
+// viscosity ratio, tau_nu(rho) = tauV + (rho - rho_V) dtau clamped to
+// [tau_lo, tau_hi] and the rates formed per node.
+template <typename T>
+struct Visc {
+  T knu, hnu2, hnu4;
+  T tauV, dtau, tau_lo, tau_hi, rho_V;
+};
+
+// The part of an instance descriptor fixed by its lbm_params.  The step
+// kernels take it by value as a kernel parameter (one launch per distinct
+// parameter set of a batch): warp-uniform constants then sit in the constant
+// bank and enter the arithmetic as operands, without loads or registers.
+struct __align__(16) PhysDesc {
+  int wall, ghost;
+  int omega_cs2w;  // omega_alpha = cs^2 w_alpha (else w_alpha) in A(x)
   int pad_;
-  long long plane;  // nx * ny
-  void* f[2];
-  const uint16_t* flags;
-  const uint8_t* row_plain;
-  const double2* A;
-  void* Fw[2];
-  int* err;  // latched device error bits
   // Eq. (15) as psi^2 = a rho + b per branch (G < 0, c = 1)
   double rho1, rho2, aV, aM, bM, aL, bL;
   // the same as unevaluated FP32 pairs (hi, lo): per branch {a_hi, a_lo,
@@ -70,6 +76,26 @@ struct __align__(16) InstDesc {
   Consts<float> cf;
 };
 
+struct __align__(16) InstDesc {
+  int nx, ny;
+  int fsi;
+  int var_nu;  // tau_nu_L != tau_nu_V: viscosity rates per node
+  long long plane;  // nx * ny
+  void* f[2];
+  const uint16_t* flags;
+  const uint8_t* row_plain;
+  const double2* A;
+  void* Fw[2];
+  int* err;  // latched device error bits
+  Visc<double> vd;
+  Visc<float> vf;
+  PhysDesc ph;  // read by the kernels outside the step (init, fields, adjoint)
+};
+
+// bytes of InstDesc in front of ph: all that the step kernels read of it
+constexpr size_t INST_HEAD_BYTES = offsetof(InstDesc, ph);
+static_assert(INST_HEAD_BYTES % 16 == 0, "the head is copied as 16-byte words");
+
 struct WorkItem {
   int inst, x0, y0, y1;
 };
@@ -77,8 +103,11 @@ struct WorkItem {
 enum : int { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
 
 // step pipelines (launch_step's `stages` argument): block rows with register
-// prefetch, warp strips, or block rows with a TMA ring of 8 / 16 stages
-enum : int { PIPE_BLOCK = 0, PIPE_WARP = 2 };
+// prefetch, warp strips (two rows per lane with FP32 storage, one otherwise),
+// warp strips with one row per lane, or block rows with a TMA ring of 8 / 16
+// stages
+enum : int { PIPE_BLOCK = 0, PIPE_WARP = 2, PIPE_WARP1 = 3 };
+inline bool is_warp_pipe(int S) { return S == PIPE_WARP || S == PIPE_WARP1; }
 
 // D2Q9 weights of the equilibrium
 __host__ __device__ constexpr double w_eq(int a) {
@@ -105,9 +134,11 @@ cudaError_t launch_adjoint_step(const InstDesc& h, const InstDesc* d_inst, const
 lbm_status set_error(lbm_status s, const char* fmt, ...);
 
 // launchers (lbm_kernels.cu)
-cudaError_t launch_step(int prec, const InstDesc* d_inst, const WorkItem* d_items, int n_items,
-                        int parity, int bx, int stages, cudaStream_t s);
-cudaError_t launch_step_persistent(int prec, const InstDesc* d_inst, const WorkItem* d_items,
+cudaError_t launch_step(int prec, const PhysDesc& ph, const InstDesc* d_inst,
+                        const WorkItem* d_items, int n_items, int parity, int bx, int stages,
+                        cudaStream_t s);
+cudaError_t launch_step_persistent(int prec, const PhysDesc& ph, const InstDesc* d_inst,
+                                   const WorkItem* d_items,
                                    int n_items, int parity0, long n_steps, int bx, int stages,
                                    unsigned* d_barrier, cudaStream_t s);
 int persistent_max_blocks(int prec, int bx, int stages);

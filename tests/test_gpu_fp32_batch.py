@@ -68,7 +68,9 @@ def test_batch_matches_oracle(cuda):
 
 @pytest.mark.parametrize("launch", [dict(persistent=True), dict(graph=True),
                                     dict(bx=64, h=9, persistent=True), dict(stages=2),
-                                    dict(stages=2, bx=64, h=11), dict(stages=2, graph=True)])
+                                    dict(stages=2, bx=64, h=11), dict(stages=2, graph=True),
+                                    dict(stages=3), dict(stages=3, bx=96, h=7),
+                                    dict(stages=2, bx=256, h=1), dict(stages=2, bx=32, h=4)])
 def test_launch_modes_bitwise(cuda, launch):
     specs = _batch_specs("fp32")
     ref = _run_batch(specs, 120)
@@ -130,7 +132,8 @@ def _batch_specs_w4(prec="fp32"):
 @pytest.mark.parametrize("launch", [dict(stages=8), dict(stages=16, bx=128),
                                     dict(stages=8, bx=32, h=5), dict(stages=8, persistent=True),
                                     dict(stages=8, bx=64, h=7, persistent=True),
-                                    dict(stages=2), dict(stages=2, bx=256, h=3), dict(stages=2, bx=32, h=2)])
+                                    dict(stages=2), dict(stages=2, bx=256, h=3), dict(stages=2, bx=32, h=2),
+                                    dict(stages=3), dict(stages=3, bx=64, h=5)])
 def test_tma_pipeline_bitwise_equal_to_register_pipeline(cuda, prec, launch):
     specs = _batch_specs_w4(prec)
     ref = _run_batch(specs, 130, dict(stages=1))
