@@ -391,8 +391,8 @@ static lbm_status build_items(lbm_ctx* c) {
     if (maxnx + 2 <= 512) bx = ((maxnx + 2 + 31) / 32) * 32;
     else bx = 256;
   }
-  // warp strips: 8 warps per block; 4 for two rows per lane (about 150
-  // registers a thread: three such blocks fit an SM, two of 8 warps would not)
+  // warp strips: 8 warps per block; 4 for two rows per lane (128 registers
+  // a thread: four blocks, 16 warps per SM)
   if (warp_mode && c->bx <= 0) bx = two_rows ? 128 : 256;
   bx = std::max(32, std::min(warp_mode ? 256 : 512, ((bx + 31) / 32) * 32));
   const int cols = warp_mode ? 30 : bx - 2;
