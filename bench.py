@@ -68,7 +68,8 @@ def sweep_instances(prec, world_size=1, rank=0):
     out = []
     for c in inputs.sweep_cases(world_size, rank):
         p = default_params(prec=prec, tau_nu_L=c["tau_nu_L"], tau_nu_V=c["tau_nu_V"])
-        out.append(dict(nx=NX, ny=NY, params=p, solid=solid, fsi=c["fsi"], gw=c["gw"]))
+        out.append(dict(nx=NX, ny=NY, params=p, solid=solid, fsi=c["fsi"],
+                        gw=inputs.wall_gw(solid, c["gw"])))
     return out
 
 
@@ -355,7 +356,7 @@ def cpu_baseline(args, budget_s=None):
     while time.perf_counter() - t0 < budget and k < len(cases):
         c = cases[k]
         p = oracle.paper_params(tau_nu_L=c["tau_nu_L"], tau_nu_V=c["tau_nu_V"])
-        o = oracle.Lattice(NX, NY, p, solid, c["fsi"], c["gw"])
+        o = oracle.Lattice(NX, NY, p, solid, c["fsi"], inputs.wall_gw(solid, c["gw"]))
         o.init_droplet(NX / 2, y_w, R, inputs.SWEEP_WIDTH)
         ts = time.perf_counter()
         steps = 0

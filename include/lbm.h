@@ -72,12 +72,17 @@ typedef enum { LBM_WALL_NEQ_ONNODE = 0, LBM_WALL_HALFWAY_BB = 1 } lbm_wall;
    node next to it along the wall normal, MIRROR the psi of the fluid node
    two rows away (both need whole solid rows).  ZERO gives solid nodes
    psi = 0.  SKIP does not apply Eq. (7) at fluid nodes that have a solid
-   neighbour (Sec. III.B, rough surfaces); any mask. */
+   neighbour (Sec. III.B, rough surfaces); any mask.  MEAN gives a solid
+   node the mean psi of the fluid nodes next to it along the axes (up, down,
+   right, left), a ghost layer for walls of any shape such as the pillars of
+   Sec. III.B; on a flat wall it equals COPY.  lbm_adjoint supports COPY,
+   MIRROR, ZERO and SKIP. */
 typedef enum {
   LBM_GHOST_COPY = 0,
   LBM_GHOST_MIRROR = 1,
   LBM_GHOST_ZERO = 2,
-  LBM_GHOST_SKIP = 3
+  LBM_GHOST_SKIP = 3,
+  LBM_GHOST_MEAN = 4
 } lbm_ghost;
 
 /* Weights omega_alpha of Eqs. (10), (11), (14).  LBM_OMEGA_W: w_alpha of

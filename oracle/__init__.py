@@ -15,7 +15,7 @@ from . import build as _build
 Q = 9
 FSI = {"density": 0, "psi": 1, "modified": 2}
 WALL = {"neq": 0, "bb": 1}
-GHOST = {"copy": 0, "mirror": 1, "zero": 2, "skip": 3}
+GHOST = {"copy": 0, "mirror": 1, "zero": 2, "skip": 3, "mean": 4}
 OMEGA = {"w": 0, "cs2w": 1}
 
 

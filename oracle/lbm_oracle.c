@@ -34,7 +34,9 @@
  *   - ghost psi: COPY takes psi of the fluid node next to the solid node
  *     along the wall normal, MIRROR the node two rows away, ZERO uses 0;
  *     SKIP does not apply Eq. (7) at fluid nodes touching solid (Sec. III.B:
- *     rough surfaces without a ghost layer).
+ *     rough surfaces without a ghost layer); MEAN takes the mean psi of the
+ *     fluid nodes next to the solid node along the axes, COPY extended to
+ *     walls of any shape (a ghost layer below rough surfaces, Sec. III.B).
  *   - tau_nu varies linearly with rho between rho_V and rho_L (clamped)
  *     when the liquid and vapour values differ (Sec. III.C).
  *   - M is the orthogonal D2Q9 basis whose rows give the equilibria of
@@ -269,6 +271,21 @@ static void macroscopic(oracle_lbm* o) {
       } else if (p->ghost == ORC_GHOST_MIRROR) {
         if (up) g = o->psi[nid(o, x, y + 2)];
         else if (dn) g = o->psi[nid(o, x, y - 2)];
+      } else if (p->ghost == ORC_GHOST_MEAN) {
+        /* any wall shape: the mean psi of the fluid nodes next to the solid
+           node along the axes (up, down, right, left); on a flat wall this
+           is COPY */
+        const int gx[4] = {0, 0, 1, -1}, gy[4] = {1, -1, 0, 0};
+        double sum = 0.0;
+        int n = 0;
+        for (int k = 0; k < 4; ++k) {
+          size_t j = nid(o, x + gx[k], y + gy[k]);
+          if (!o->s[j]) {
+            sum += o->psi[j];
+            ++n;
+          }
+        }
+        if (n > 0) g = sum / n;
       }
       o->psi[i] = g;
     }

@@ -28,7 +28,8 @@ enum { ORC_FSI_DENSITY = 0, ORC_FSI_PSI = 1, ORC_FSI_MODIFIED = 2 };
 enum { ORC_WALL_NEQ = 0, ORC_WALL_BB = 1 };
 /* Pseudopotential assigned to solid nodes when Eq. (7) is applied at walls;
    SKIP: Eq. (7) not applied at fluid nodes with a solid neighbour. */
-enum { ORC_GHOST_COPY = 0, ORC_GHOST_MIRROR = 1, ORC_GHOST_ZERO = 2, ORC_GHOST_SKIP = 3 };
+enum { ORC_GHOST_COPY = 0, ORC_GHOST_MIRROR = 1, ORC_GHOST_ZERO = 2, ORC_GHOST_SKIP = 3,
+       ORC_GHOST_MEAN = 4 };
 /* Weights omega_alpha of the fluid-solid force, Eqs. (10), (11), (14).
    ORC_OMEGA_W: omega_alpha = w_alpha of Eq. (7) (1/3, 1/12); the G_w values
    printed with Figs. 2-4 give the printed angles under this choice.

@@ -139,7 +139,7 @@ static lbm_status validate_params(const lbm_params* p) {
   if (!(p->sigma >= 0.0)) return fail(LBM_ERR_ARG, "sigma must be >= 0");
   if (!(p->rho_L > p->rho_V && p->rho_V > 0.0)) return fail(LBM_ERR_ARG, "need rho_L > rho_V > 0");
   if ((int)p->wall < 0 || (int)p->wall > 1) return fail(LBM_ERR_ARG, "unknown wall %d", (int)p->wall);
-  if ((int)p->ghost < 0 || (int)p->ghost > 3) return fail(LBM_ERR_ARG, "unknown ghost %d", (int)p->ghost);
+  if ((int)p->ghost < 0 || (int)p->ghost > 4) return fail(LBM_ERR_ARG, "unknown ghost %d", (int)p->ghost);
   if ((int)p->omega < 0 || (int)p->omega > 1) return fail(LBM_ERR_ARG, "unknown omega %d", (int)p->omega);
   if ((int)p->prec < 0 || (int)p->prec > 2) return fail(LBM_ERR_ARG, "unknown precision %d", (int)p->prec);
   if (!isfinite(p->rho_ref)) return fail(LBM_ERR_ARG, "rho_ref must be finite");
@@ -173,8 +173,17 @@ static lbm_status build_flags(Inst& I) {
       uint16_t fl = 0;
       if (S(x, y)) {
         fl |= NF_SELF_SOLID;
-        if (!S(x, y + 1)) fl |= NF_GHOST_UP;
-        else if (!S(x, y - 1)) fl |= NF_GHOST_DOWN;
+        if (I.p.ghost == LBM_GHOST_MEAN) {
+          // every axis neighbour that is fluid contributes to the mean
+          if (!S(x, y + 1)) fl |= NF_GHOST_UP;
+          if (!S(x, y - 1)) fl |= NF_GHOST_DOWN;
+          if (!S(x + 1, y)) fl |= NF_GHOST_RIGHT;
+          if (!S(x - 1, y)) fl |= NF_GHOST_LEFT;
+        } else if (!S(x, y + 1)) {
+          fl |= NF_GHOST_UP;
+        } else if (!S(x, y - 1)) {
+          fl |= NF_GHOST_DOWN;
+        }
         if (I.p.ghost == LBM_GHOST_MIRROR) {
           if ((fl & NF_GHOST_UP) && S(x, y + 2))
             return fail(LBM_ERR_ARG, "MIRROR ghost needs two fluid rows above solid row %d", y);
@@ -948,6 +957,8 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, long T, double theta_target, doubl
   if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
   if (c->inst.size() != 1) return fail(LBM_ERR_ARG, "lbm_adjoint needs a single-lattice context");
   if (c->prec != LBM_FP64) return fail(LBM_ERR_ARG, "lbm_adjoint needs LBM_FP64");
+  if (c->inst[0].p.ghost == LBM_GHOST_MEAN)
+    return fail(LBM_ERR_ARG, "lbm_adjoint supports the COPY, MIRROR, ZERO and SKIP ghosts");
   if (T < 1) return fail(LBM_ERR_ARG, "T must be >= 1");
   Inst& I = c->inst[0];
   if (I.p.tau_nu_L != I.p.tau_nu_V)

@@ -31,6 +31,8 @@ enum : uint16_t {
   NF_NEQ_TOP = 1u << 11,     // fluid, solid directly above, mirrored rule
   NF_GHOST_UP = 1u << 12,    // solid, fluid directly above (ghost psi source)
   NF_GHOST_DOWN = 1u << 13,  // solid, fluid directly below
+  NF_GHOST_RIGHT = 1u << 14, // solid, fluid at x + 1 (MEAN ghost only)
+  NF_GHOST_LEFT = 1u << 15,  // solid, fluid at x - 1 (MEAN ghost only)
 };
 
 template <typename T>

@@ -15,6 +15,15 @@ def flat_walls(nx, ny):
     return s
 
 
+def wall_gw(solid, gw):
+    """G_w field for a mask whose top row is a wall: gw on every solid node
+    except the top row y = ny - 1, which is neutral (G_w = 0), so that only
+    the wall the droplet sits on is wetting or non-wetting."""
+    g = np.where(np.asarray(solid) != 0, float(gw), 0.0)
+    g[-1, :] = 0.0
+    return g
+
+
 def wall_height(ghost="copy"):
     """Height of the wall surface for the contact-angle fit with flat_walls:
     half a lattice spacing above the solid row for COPY ghosts and bounce-back,

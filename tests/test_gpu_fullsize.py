@@ -29,7 +29,8 @@ def _oracle(k):
     c = inputs.sweep_cases()[k]
     oracle.set_threads(8)
     p = oracle.paper_params(tau_nu_L=c["tau_nu_L"], tau_nu_V=c["tau_nu_V"])
-    o = oracle.Lattice(NX, NY, p, inputs.flat_walls(NX, NY), c["fsi"], c["gw"])
+    solid = inputs.flat_walls(NX, NY)
+    o = oracle.Lattice(NX, NY, p, solid, c["fsi"], inputs.wall_gw(solid, c["gw"]))
     o.init_droplet(NX / 2, 0.5, R, inputs.SWEEP_WIDTH)
     o.step(STEPS)
     return o.fields()

@@ -65,13 +65,15 @@ def test_persistent_needs_one_parameter_set(cuda):
     c.set_launch(stages=1, persistent=True)
 
 
+@pytest.mark.parametrize("ghost", ["skip", "mean"])
 @pytest.mark.parametrize("launch", [dict(stages=2), dict(stages=2, bx=64, h=7),
-                                    dict(stages=2, bx=256, h=3), dict(stages=3, h=9)])
-def test_pair_strips_on_pillars_bitwise(cuda, launch):
+                                    dict(stages=2, bx=256, h=3), dict(stages=3, h=9),
+                                    dict(stages=8, bx=64, h=5)])
+def test_pair_strips_on_pillars_bitwise(cuda, launch, ghost):
     nx, ny = 92, 61
     solid = inputs.pillars(nx, ny, height=10, width=6, gap=3)
     drop = (45.0, 30.0, 15.0, 2.0)
-    kw = dict(prec="fp32", wall="bb", ghost="skip", **RATIO2)
+    kw = dict(prec="fp32", wall="bb", ghost=ghost, **RATIO2)
     a = run_gpu(nx, ny, 300, "modified", 0.3, solid, drop, launch=dict(stages=1), **kw)
     b = run_gpu(nx, ny, 300, "modified", 0.3, solid, drop, launch=launch, **kw)
     assert np.array_equal(a.populations(), b.populations())

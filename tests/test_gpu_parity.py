@@ -48,14 +48,18 @@ def test_tile_shape_is_bit_identical(cuda):
         assert np.array_equal(got, ref), (bx, h)
 
 
-@pytest.mark.parametrize("fsi,gw", [("density", 0.2), ("modified", 0.3)])
-def test_rough_surface_bounce_back(cuda, fsi, gw):
-    # square pillars (Sec. III.B): halfway bounce-back, Eq. (7) not applied
-    # next to the wall, droplet resting on the pillar tops
+@pytest.mark.parametrize("fsi,gw,ghost", [("density", 0.2, "skip"), ("modified", 0.3, "skip"),
+                                          ("density", 0.2, "mean"), ("modified", 0.3, "mean"),
+                                          ("psi", 1.5, "mean")])
+def test_rough_surface_bounce_back(cuda, fsi, gw, ghost):
+    # square pillars (Sec. III.B): halfway bounce-back, Eq. (7) either not
+    # applied next to the wall or applied with the MEAN ghost layer, droplet
+    # resting on the pillar tops
     nx, ny = 90, 60
     solid = inputs.pillars(nx, ny, height=10, width=6, gap=3)
     drop = (45.0, 30.0, 15.0, 2.0)
-    o = run_oracle(nx, ny, 400, fsi, gw, solid, drop, wall="bb", ghost="skip")
-    g = run_gpu(nx, ny, 400, fsi, gw, solid, drop, wall="bb", ghost="skip")
+    gwf = inputs.wall_gw(solid, gw)
+    o = run_oracle(nx, ny, 400, fsi, gwf, solid, drop, wall="bb", ghost=ghost)
+    g = run_gpu(nx, ny, 400, fsi, gwf, solid, drop, wall="bb", ghost=ghost)
     e = field_errors(g, o, solid)
     assert e["rho"] <= 1e-10 and e["f"] <= 1e-10 and e["u"] <= 1e-10, e

@@ -54,7 +54,8 @@ def _run_sessile(args):
     from paper_1410_2569_gb300 import inputs
     oracle.set_threads(1)
     nx, ny = 300, 100
-    o = oracle.Lattice(nx, ny, oracle.paper_params(), inputs.flat_walls(nx, ny), fsi, gw)
+    solid = inputs.flat_walls(nx, ny)
+    o = oracle.Lattice(nx, ny, oracle.paper_params(), solid, fsi, inputs.wall_gw(solid, gw))
     o.init_droplet(nx / 2, y0, 30.0, 2.0)
     o.step(STEPS)
     return o.diagnostics(0.5, nx / 2, 3.0)

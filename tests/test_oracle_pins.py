@@ -211,6 +211,40 @@ def test_skip_removes_fluid_fluid_force_next_to_wall():
     assert np.abs(fl["Fy"][2]).max() > 1.0  # Eq. (7) still acts one row up
 
 
+def test_mean_ghost_is_copy_on_flat_walls():
+    """MEAN (a ghost layer for walls of any shape) reduces to the COPY ghost
+    of Sec. III.A on flat walls: the same populations, bit for bit."""
+    nx, ny = 48, 32
+    solid = inputs.flat_walls(nx, ny)
+    runs = {}
+    for ghost in ("copy", "mean"):
+        o = oracle.Lattice(nx, ny, oracle.paper_params(ghost=ghost, wall="bb"), solid,
+                           "modified", inputs.wall_gw(solid, 0.2))
+        o.init_droplet(24, 0.5, 10, 2.0)
+        o.step(200)
+        runs[ghost] = o.populations()
+    assert np.array_equal(runs["copy"], runs["mean"])
+
+
+def test_mean_ghost_on_pillars():
+    """On square pillars a solid corner node takes the mean psi of its two
+    fluid neighbours (above and beside), a side node the psi of its one
+    fluid neighbour, and a node inside a pillar psi = 0."""
+    nx, ny = 27, 24
+    solid = inputs.pillars(nx, ny, height=6, width=6, gap=3)
+    o = oracle.Lattice(nx, ny, oracle.paper_params(wall="bb", ghost="mean"), solid, "density",
+                       inputs.wall_gw(solid, 0.1))
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    o.set_density(1.0 + 0.5 * 499.0 * (1 - np.tanh(((xx - 13.0) ** 2 + (yy - 12.0) ** 2) ** 0.5 - 6.0)))
+    psi = o.fields()["psi"]
+    top = 6  # pillar rows 1..6, columns 0..5, 9..14, 18..23
+    assert psi[top, 9] == (psi[top + 1, 9] + psi[top, 8]) / 2  # top-left corner
+    assert psi[top, 14] == (psi[top + 1, 14] + psi[top, 15]) / 2  # top-right corner
+    assert psi[top, 11] == psi[top + 1, 11]  # top face
+    assert psi[3, 9] == psi[3, 8] and psi[3, 14] == psi[3, 15]  # side faces
+    assert psi[3, 11] == 0.0  # inside the pillar
+
+
 def test_wall_rule_gives_zero_momentum():
     """After the wall rule of Sec. III.A, sum_a e_a f_a + F/2 = 0 at every wall
     node, with F the force of that node's collision."""
@@ -231,7 +265,7 @@ def test_wall_rule_gives_zero_momentum():
 
 # ---------------------------------------------------------------- invariants
 
-@pytest.mark.parametrize("case", ["periodic", "bb_flat", "bb_pillars"])
+@pytest.mark.parametrize("case", ["periodic", "bb_flat", "bb_pillars", "bb_pillars_mean"])
 def test_mass_conservation(case):
     nx, ny = 48, 40
     if case == "periodic":
@@ -239,8 +273,9 @@ def test_mass_conservation(case):
     elif case == "bb_flat":
         solid, over = inputs.flat_walls(nx, ny), dict(wall="bb")
     else:
+        ghost = "mean" if case.endswith("mean") else "zero"
         solid, over = inputs.pillars(nx, ny, height=6, width=4, gap=3), dict(wall="bb",
-                                                                            ghost="zero")
+                                                                            ghost=ghost)
     o = oracle.Lattice(nx, ny, oracle.paper_params(**over), solid, "psi", 0.8)
     o.init_droplet(24, 12, 9, 2.0)
     m0 = o.fields()["rho"][solid == 0].sum()
