@@ -207,6 +207,20 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, int inst, double* f, int dst_is_dev
 lbm_status lbm_diagnostics(lbm_ctx* ctx, int inst, double y_w, double x_ref, double d_min,
                            lbm_diag* out);
 
+/* Spreading (contact) radius of a droplet on a wall (dynamic wetting,
+   Sec. III.A, Fig. 7), from the density of instance inst at the current
+   time along node row `row` (the first fluid row above a bottom wall).
+   From the column nearest x_ref the row is walked right and left to the
+   first node below `level`; each crossing is interpolated linearly between
+   that node and the one before it, and solid nodes count as below the
+   level.  *r_out = (x_right - x_left) / 2 in lattice units: 0 when rho at
+   the start column is below the level (no contact), nx / 2 when the whole
+   row is above it.  level <= 0 means (rho_L + rho_V) / 2 of the instance.
+   LBM_ERR_ARG for a row outside [0, ny) or a non-finite x_ref.
+   Synchronises. */
+lbm_status lbm_contact_radius(lbm_ctx* ctx, int inst, int row, double level, double x_ref,
+                              double* r_out);
+
 /* Replaces the G_w field of instance inst ([ny][nx] host, read on solid
    nodes) and rebuilds the wall vectors of the fluid-solid force. */
 lbm_status lbm_set_gw_field(lbm_ctx* ctx, int inst, const double* gw);

@@ -70,6 +70,9 @@ def lib():
         L.oracle_contact_angle.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_void_p,
                                            ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double, ctypes.POINTER(OracleDiag)]
+        L.oracle_contact_radius.restype = ctypes.c_double
+        L.oracle_contact_radius.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_void_p,
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_double]
         L.oracle_mrt_matrices.argtypes = [dp, dp]
         L.oracle_p_eos.restype = ctypes.c_double
         L.oracle_p_eos.argtypes = [ctypes.POINTER(OracleParams), ctypes.c_double]
@@ -131,6 +134,15 @@ def contact_angle(rho, solid, level, y_w, x_ref, d_min=3.0):
     lib().oracle_contact_angle(nx, ny, _dptr(rho), None if s is None else s.ctypes.data,
                                level, y_w, x_ref, d_min, ctypes.byref(d))
     return d.as_dict()
+
+
+def contact_radius(rho, solid, row, level, x_ref):
+    """Spreading radius along node row `row` (oracle_contact_radius)."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    ny, nx = rho.shape
+    s = None if solid is None else np.ascontiguousarray(solid, dtype=np.uint8)
+    return lib().oracle_contact_radius(nx, ny, _dptr(rho), None if s is None else s.ctypes.data,
+                                       int(row), float(level), float(x_ref))
 
 
 class Lattice:

@@ -488,6 +488,36 @@ void oracle_set_populations(oracle_lbm* o, const double* f, const double* unused
 }
 
 /* ---------------- diagnostics and the contact angle ---------------- */
+/* Spreading radius of a droplet on a wall (dynamic wetting, Sec. III.A and
+ * Fig. 7): on node row `row`, starting at the column nearest x_ref, the
+ * first node on the right and on the left whose density is below `level`
+ * (solid nodes count as 0); the level crossing lies between it and the
+ * previous node, by linear interpolation.  The radius is half the distance
+ * between the two crossings; 0 if the start node is below the level, nx/2 if
+ * no node of the row is. */
+double oracle_contact_radius(int nx, int ny, const double* rho, const uint8_t* solid, int row,
+                             double level, double x_ref) {
+  (void)ny;
+  const double* r = rho + (size_t)row * nx;
+  const uint8_t* s = solid ? solid + (size_t)row * nx : NULL;
+  int x0 = (int)floor(x_ref + 0.5);
+  x0 = ((x0 % nx) + nx) % nx;
+#define RHO_AT(x) ((s && s[x]) ? 0.0 : r[x])
+  if (!(RHO_AT(x0) >= level)) return 0.0;
+  double right = -1.0, left = -1.0;
+  for (int d = 1; d <= nx && right < 0.0; ++d) {
+    const int xb = (x0 + d) % nx, xa = (x0 + d - 1) % nx;
+    if (RHO_AT(xb) < level) right = (d - 1) + (level - RHO_AT(xa)) / (RHO_AT(xb) - RHO_AT(xa));
+  }
+  for (int d = 1; d <= nx && left < 0.0; ++d) {
+    const int xb = ((x0 - d) % nx + nx) % nx, xa = ((x0 - d + 1) % nx + nx) % nx;
+    if (RHO_AT(xb) < level) left = (d - 1) + (level - RHO_AT(xa)) / (RHO_AT(xb) - RHO_AT(xa));
+  }
+#undef RHO_AT
+  if (right < 0.0 || left < 0.0) return 0.5 * nx;
+  return 0.5 * (right + left);
+}
+
 /* Level-set points of rho = level on grid edges between fluid nodes, linear
  * interpolation; x unwrapped about x_ref; points closer than d_min to the wall
  * height y_w dropped; Kasa circle fit x^2 + y^2 + D x + E y + F = 0 by least

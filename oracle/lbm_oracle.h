@@ -79,6 +79,9 @@ void oracle_set_populations(oracle_lbm* o, const double* f, const double* F_prev
    reference x_ref, points closer than d_min to the wall discarded */
 int oracle_diagnostics(oracle_lbm* o, double y_w, double x_ref, double d_min, oracle_diag* d);
 /* circle fit on an explicit density field (used by the adjoint loss) */
+/* spreading (contact) radius along node row `row`, Sec. III.A / Fig. 7 */
+double oracle_contact_radius(int nx, int ny, const double* rho, const uint8_t* solid, int row,
+                             double level, double x_ref);
 int oracle_contact_angle(int nx, int ny, const double* rho, const uint8_t* solid, double level,
                          double y_w, double x_ref, double d_min, oracle_diag* d);
 /* the 9x9 transformation matrix M and its inverse, row-major */

@@ -745,6 +745,26 @@ extern "C" lbm_status lbm_get_fields(lbm_ctx* c, int inst, double* rho, double* 
   return lbm_sync(c);
 }
 
+extern "C" lbm_status lbm_contact_radius(lbm_ctx* c, int inst, int row, double level,
+                                         double x_ref, double* r_out) {
+  lbm_status st = check_inst(c, inst);
+  if (st != LBM_OK) return st;
+  if (!r_out) return fail(LBM_ERR_ARG, "r_out is NULL");
+  const Inst& I = c->inst[inst];
+  if (row < 0 || row >= I.ny) return fail(LBM_ERR_ARG, "row %d outside [0, %d)", row, I.ny);
+  if (!isfinite(x_ref)) return fail(LBM_ERR_ARG, "x_ref must be finite");
+  if (!(level > 0.0)) level = 0.5 * (I.p.rho_L + I.p.rho_V);
+  st = ensure_scratch(c, (size_t)I.nx * I.ny);
+  if (st != LBM_OK) return st;
+  int xi = (int)floor(x_ref + 0.5) % I.nx;
+  if (xi < 0) xi += I.nx;
+  // row densities in d_rho[0, nx), the radius in d_rho[nx]
+  CK(launch_row_rho(c->prec, I.desc, c->d_desc + inst, c->parity, row, c->d_rho, c->stream));
+  CK(launch_contact_scan(c->d_rho, I.nx, level, xi, c->d_rho + I.nx, c->stream));
+  CK(cudaMemcpyAsync(r_out, c->d_rho + I.nx, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return lbm_sync(c);
+}
+
 extern "C" lbm_status lbm_get_populations(lbm_ctx* c, int inst, double* f, int dst_is_device) {
   lbm_status st = check_inst(c, inst);
   if (st != LBM_OK) return st;

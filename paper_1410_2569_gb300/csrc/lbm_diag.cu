@@ -52,6 +52,42 @@ __device__ __forceinline__ bool is_solid(const uint8_t* mask, long long i) {
   return mask != nullptr && mask[i] != 0;
 }
 
+// Spreading (contact) radius along one row (Sec. III.A, Fig. 7): from the
+// node xi, walk right and left to the first node below the level; the
+// crossing is interpolated linearly between that node and the one before
+// it.  One thread: a row holds at most a few thousand nodes and the call is
+// a diagnostic taken every few steps.
+__global__ void k_contact_scan(const double* __restrict__ row, int nx, double level, int xi,
+                               double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (!(row[xi] >= level)) {
+    out[0] = 0.0;  // the droplet does not touch the row at xi
+    return;
+  }
+  double xr = -1.0, xl = -1.0;
+  for (int k = 0; k < nx; ++k) {
+    const double a = row[(xi + k) % nx], b = row[(xi + k + 1) % nx];
+    if (b < level) {
+      xr = k + (level - a) / (b - a);
+      break;
+    }
+  }
+  for (int k = 0; k < nx; ++k) {
+    const double a = row[((xi - k) % nx + nx) % nx], b = row[((xi - k - 1) % nx + nx) % nx];
+    if (b < level) {
+      xl = k + (level - a) / (b - a);
+      break;
+    }
+  }
+  out[0] = (xr < 0.0 || xl < 0.0) ? 0.5 * nx : 0.5 * (xr + xl);
+}
+
+cudaError_t launch_contact_scan(const double* d_row, int nx, double level, int xi, double* d_out,
+                                cudaStream_t s) {
+  k_contact_scan<<<1, 32, 0, s>>>(d_row, nx, level, xi, d_out);
+  return cudaGetLastError();
+}
+
 // mode 0: statistics and fit sums; mode 1: sum of squared radial residuals
 template <int MODE, typename MaskT>
 __global__ void __launch_bounds__(DIAG_THREADS)

@@ -147,6 +147,11 @@ int persistent_max_blocks(int prec, int bx, int stages);
 cudaError_t launch_barrier_selftest(unsigned* d_bar, int* d_err, double seconds, cudaStream_t s);
 cudaError_t launch_init(int prec, const InstDesc& h_inst, const InstDesc* d_inst, int parity,
                         const double* d_rho0, cudaStream_t s);
+cudaError_t launch_row_rho(int prec, const InstDesc& h_inst, const InstDesc* d_inst, int parity,
+                           int row, double* d_out, cudaStream_t s);
+// contact radius from one row of rho (lbm_diag.cu); writes out[0]
+cudaError_t launch_contact_scan(const double* d_row, int nx, double level, int xi, double* d_out,
+                                cudaStream_t s);
 cudaError_t launch_macro(int prec, const InstDesc& h_inst, const InstDesc* d_inst, int parity,
                          double* d_rho, double* d_psi, double* d_ux, double* d_uy, double* d_f,
                          cudaStream_t s);

@@ -177,6 +177,16 @@ class Lattice:
         out["status"] = st
         return out
 
+    def contact_radius(self, inst=0, row=1, level=0.0, x_ref=None):
+        """Spreading radius along node row `row` (lbm_contact_radius); level
+        0 means (rho_L + rho_V) / 2."""
+        ny, nx = self.shapes[inst]
+        r = ctypes.c_double()
+        check(self._L.lbm_contact_radius(self._h, inst, int(row), float(level),
+                                         float(nx / 2 if x_ref is None else x_ref),
+                                         ctypes.byref(r)))
+        return r.value
+
     def set_gw_field(self, gw, inst=0):
         g = np.ascontiguousarray(gw, dtype=np.float64)
         check(self._L.lbm_set_gw_field(self._h, inst, g.ctypes.data))

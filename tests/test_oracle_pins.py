@@ -245,6 +245,31 @@ def test_mean_ghost_on_pillars():
     assert psi[3, 11] == 0.0  # inside the pillar
 
 
+def test_contact_radius_on_ramps():
+    """Spreading radius (Fig. 7) on rows whose level crossings follow by hand
+    from linear interpolation between nodes."""
+    nx, ny = 40, 4
+    rho = np.zeros((ny, nx))
+    rho[1, 15:26] = 10.0  # liquid on columns 15..25, vapour 0 elsewhere
+    # crossings of level 5: 14.5 on the left, 25.5 on the right
+    assert oracle.contact_radius(rho, None, 1, 5.0, 20.0) == 5.5
+    # a ramp: rho(26) = 8, rho(27) = 2 moves the right crossing to 26.5
+    rho[1, 26], rho[1, 27] = 8.0, 2.0
+    assert abs(oracle.contact_radius(rho, None, 1, 5.0, 20.0) - 6.0) < 1e-15
+    # across the periodic seam: liquid on columns 36..39 and 0..3
+    w = np.zeros((ny, nx))
+    w[1, 36:] = 10.0
+    w[1, :4] = 10.0
+    assert oracle.contact_radius(w, None, 1, 5.0, 0.0) == 4.0
+    assert oracle.contact_radius(w, None, 1, 5.0, 20.0) == 0.0  # start in vapour
+    full = np.full((ny, nx), 10.0)
+    assert oracle.contact_radius(full, None, 1, 5.0, 3.0) == nx / 2
+    # a solid node counts as below the level
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[1, 22] = 1
+    assert oracle.contact_radius(rho, solid, 1, 5.0, 20.0) == 0.5 * ((21.5 - 20) + (20 - 14.5))
+
+
 def test_wall_rule_gives_zero_momentum():
     """After the wall rule of Sec. III.A, sum_a e_a f_a + F/2 = 0 at every wall
     node, with F the force of that node's collision."""
