@@ -176,8 +176,17 @@ lbm_status lbm_instance_size(const lbm_ctx* ctx, int inst, int* nx, int* ny);
 lbm_status lbm_init_droplet(lbm_ctx* ctx, int inst, double x0, double y0, double R,
                             double width);
 
-/* Fluid at rest with the density field rho [ny][nx] (host or device FP64). */
+/* Fluid at rest with the density field rho [ny][nx] (host or device FP64).
+   Resets the step counter.  Synchronises. */
 lbm_status lbm_set_density(lbm_ctx* ctx, int inst, const double* rho, int src_is_device);
+
+/* lbm_set_density without synchronising: the copy and the initialisation
+   are enqueued on the context's stream and the call returns.  rho must stay
+   valid and unchanged until the copy has run (lbm_sync); page-locked host
+   memory lets the copy run asynchronously (a pageable buffer is copied
+   before the call returns).  Errors of the enqueued work surface at the next
+   synchronising call. */
+lbm_status lbm_set_density_async(lbm_ctx* ctx, int inst, const double* rho, int src_is_device);
 
 /* Advances every instance by n time steps.  Asynchronous: returns after
    enqueueing on the context's stream. */
@@ -193,6 +202,14 @@ long lbm_time(const lbm_ctx* ctx);
    Synchronises. */
 lbm_status lbm_get_fields(lbm_ctx* ctx, int inst, double* rho, double* ux, double* uy,
                           int dst_is_device);
+
+/* lbm_get_fields without synchronising: the field kernels and the copies
+   are enqueued on the context's stream; the outputs hold the fields after
+   lbm_sync.  Calls for several instances may be queued back to back (the
+   context's scratch fields are reused in stream order).  Page-locked host
+   outputs let the copies overlap the caller. */
+lbm_status lbm_get_fields_async(lbm_ctx* ctx, int inst, double* rho, double* ux, double* uy,
+                                int dst_is_device);
 
 /* Populations f_alpha(x, t) after streaming and the wall rule (the state
    Eq. (6) is evaluated on), FP64 [9][ny][nx]; FP32 storage is shifted back.

@@ -608,7 +608,9 @@ static lbm_status set_density_dev(lbm_ctx* c, int inst, const double* d_rho0) {
   return LBM_OK;
 }
 
-extern "C" lbm_status lbm_set_density(lbm_ctx* c, int inst, const double* rho, int src_is_device) {
+// the copy into the scratch field and the initialisation kernel, enqueued;
+// a later call reuses the scratch only after these in stream order
+static lbm_status enqueue_set_density(lbm_ctx* c, int inst, const double* rho, int src_is_device) {
   lbm_status st = check_inst(c, inst);
   if (st != LBM_OK) return st;
   if (!rho) return fail(LBM_ERR_ARG, "rho is NULL");
@@ -619,9 +621,20 @@ extern "C" lbm_status lbm_set_density(lbm_ctx* c, int inst, const double* rho, i
                      src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
   st = set_density_dev(c, inst, c->d_rho);
   if (st != LBM_OK) return st;
-  CK(cudaStreamSynchronize(c->stream));
   c->t = 0;
   return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_density(lbm_ctx* c, int inst, const double* rho, int src_is_device) {
+  lbm_status st = enqueue_set_density(c, inst, rho, src_is_device);
+  if (st != LBM_OK) return st;
+  CK(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_density_async(lbm_ctx* c, int inst, const double* rho,
+                                            int src_is_device) {
+  return enqueue_set_density(c, inst, rho, src_is_device);
 }
 
 extern "C" lbm_status lbm_init_droplet(lbm_ctx* c, int inst, double x0, double y0, double R,
@@ -727,7 +740,8 @@ extern "C" lbm_status lbm_sync(lbm_ctx* c) {
   return LBM_OK;
 }
 
-extern "C" lbm_status lbm_get_fields(lbm_ctx* c, int inst, double* rho, double* ux, double* uy,
+// the field kernels and the copies out of the scratch fields, enqueued
+static lbm_status enqueue_get_fields(lbm_ctx* c, int inst, double* rho, double* ux, double* uy,
                                      int dst_is_device) {
   lbm_status st = check_inst(c, inst);
   if (st != LBM_OK) return st;
@@ -742,7 +756,19 @@ extern "C" lbm_status lbm_get_fields(lbm_ctx* c, int inst, double* rho, double* 
   if (rho) CK(cudaMemcpyAsync(rho, c->d_rho, N * sizeof(double), k, c->stream));
   if (ux) CK(cudaMemcpyAsync(ux, c->d_ux, N * sizeof(double), k, c->stream));
   if (uy) CK(cudaMemcpyAsync(uy, c->d_uy, N * sizeof(double), k, c->stream));
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_fields(lbm_ctx* c, int inst, double* rho, double* ux, double* uy,
+                                     int dst_is_device) {
+  lbm_status st = enqueue_get_fields(c, inst, rho, ux, uy, dst_is_device);
+  if (st != LBM_OK) return st;
   return lbm_sync(c);
+}
+
+extern "C" lbm_status lbm_get_fields_async(lbm_ctx* c, int inst, double* rho, double* ux,
+                                           double* uy, int dst_is_device) {
+  return enqueue_get_fields(c, inst, rho, ux, uy, dst_is_device);
 }
 
 extern "C" lbm_status lbm_contact_radius(lbm_ctx* c, int inst, int row, double level,

@@ -118,12 +118,18 @@ class Lattice:
     def init_droplet(self, x0, y0, R, width=2.0, inst=0):
         check(self._L.lbm_init_droplet(self._h, inst, x0, y0, R, width))
 
-    def set_density(self, rho, inst=0):
+    def set_density(self, rho, inst=0, sync=True):
+        """Fluid at rest with density rho (lbm_set_density).  sync=False
+        enqueues only (lbm_set_density_async): a host array must then be
+        C-contiguous FP64 and stay unchanged until sync()."""
+        fn = self._L.lbm_set_density if sync else self._L.lbm_set_density_async
         if hasattr(rho, "data_ptr") and rho.is_cuda:
-            check(self._L.lbm_set_density(self._h, inst, ctypes.c_void_p(rho.data_ptr()), 1))
+            check(fn(self._h, inst, ctypes.c_void_p(rho.data_ptr()), 1))
         else:
+            if not sync:
+                assert rho.dtype == np.float64 and rho.flags.c_contiguous
             r = np.ascontiguousarray(rho, dtype=np.float64)
-            check(self._L.lbm_set_density(self._h, inst, r.ctypes.data, 0))
+            check(fn(self._h, inst, r.ctypes.data, 0))
 
     def step(self, n=1):
         check(self._L.lbm_step(self._h, int(n)))
@@ -138,16 +144,18 @@ class Lattice:
         check(self._L.lbm_set_launch(self._h, int(bx), int(h), int(persistent), int(graph),
                                      int(stages)))
 
-    def fields(self, inst=0, device=False, out=None):
+    def fields(self, inst=0, device=False, out=None, sync=True):
         """rho, ux, uy of instance inst: numpy (host) or torch CUDA tensors
-        (device=True); `out` may supply the three host arrays (e.g. pinned)."""
+        (device=True); `out` may supply the three host arrays (e.g. pinned).
+        With `out` and sync=False the read-back is only enqueued
+        (lbm_get_fields_async): the arrays hold the fields after sync()."""
         ny, nx = self.shapes[inst]
         if out is not None:
             for k in ("rho", "ux", "uy"):
                 a = out[k]
                 assert a.dtype == np.float64 and a.shape == (ny, nx) and a.flags.c_contiguous
-            check(self._L.lbm_get_fields(self._h, inst, *[out[k].ctypes.data
-                                                          for k in ("rho", "ux", "uy")], 0))
+            fn = self._L.lbm_get_fields if sync else self._L.lbm_get_fields_async
+            check(fn(self._h, inst, *[out[k].ctypes.data for k in ("rho", "ux", "uy")], 0))
             return out
         if device:
             import torch
