@@ -248,21 +248,22 @@ def run_ours(args, ws, rank, local):
     if not args.no_e2e and "fp32" in results:
         lat = results["fp32"]["lat"]
         n_inst = len(inputs.sweep_cases())
-        host_rho = torch.empty((NY, NX), dtype=torch.float64).pin_memory().numpy()
-        # one pinned output set per lattice: every read-back lands in its own
-        # host memory, all enqueued and waited for once
-        host_out = [{k: torch.empty((NY, NX), dtype=torch.float64).pin_memory().numpy()
-                     for k in ("rho", "ux", "uy")} for _ in range(n_inst)]
-        host_rho[:] = droplet_density(NX, NY, NX / 2, y_w, R, inputs.SWEEP_WIDTH)
+        total = lat.total_nodes
+        # pinned host fields of the whole batch, concatenated in instance
+        # order: one upload, one read-back per field, one synchronisation
+        host_rho = torch.empty(total, dtype=torch.float64).pin_memory().numpy()
+        host_out = {k: torch.empty(total, dtype=torch.float64).pin_memory().numpy()
+                    for k in ("rho", "ux", "uy")}
+        one = droplet_density(NX, NY, NX / 2, y_w, R, inputs.SWEEP_WIDTH)
+        for v in lat.split(host_rho):
+            v[:] = one
         chunk, iters = max(1, args.steps // 2), 2
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(iters):
-            for k in range(n_inst):
-                lat.set_density(host_rho, inst=k, sync=False)
+            lat.set_density_all(host_rho)
             lat.step(chunk)
-            for k in range(n_inst):
-                lat.fields(k, out=host_out[k], sync=False)
+            lat.fields_all(host_out)
             lat.sync()
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
@@ -371,10 +372,43 @@ def cpu_baseline(args, budget_s=None):
         n_inst += 1
         steps_each = max(steps_each, steps)
         k += 1
+    # the same oracle on one thread: the first sweep lattice for a short slice
+    oracle.set_threads(1)
+    c = cases[0]
+    p = oracle.paper_params(tau_nu_L=c["tau_nu_L"], tau_nu_V=c["tau_nu_V"])
+    o = oracle.Lattice(NX, NY, p, solid, c["fsi"], inputs.wall_gw(solid, c["gw"]))
+    o.init_droplet(NX / 2, y_w, R, inputs.SWEEP_WIDTH)
+    ts, steps1 = time.perf_counter(), 0
+    while time.perf_counter() - ts < max(1.0, 0.15 * budget) and steps1 < 200:
+        o.step(5)
+        steps1 += 5
+    one = NX * NY * steps1 / (time.perf_counter() - ts) / 1e6
+    oracle.set_threads(cores)
     return {"value": round(done_nodes / t_used / 1e6, 3), "unit": "MLUPS", "cores": cores,
-            "kind": "oracle",
+            "kind": "oracle", "cpu_model": cpu_model(), "value_1thread": round(one, 3),
             "sample": f"{n_inst} of the 72 sweep lattices (400x200), up to {steps_each} steps "
-                      f"each, {t_used:.1f} s of CPU time"}
+                      f"each, {t_used:.1f} s of CPU time; one thread: the first lattice, "
+                      f"{steps1} steps"}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
 
 
 def run_reference(args, ws, rank):

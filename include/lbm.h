@@ -211,6 +211,19 @@ lbm_status lbm_get_fields(lbm_ctx* ctx, int inst, double* rho, double* ux, doubl
 lbm_status lbm_get_fields_async(lbm_ctx* ctx, int inst, double* rho, double* ux, double* uy,
                                 int dst_is_device);
 
+/* The whole batch at once, without synchronising (one kernel per stage for
+   all instances, one copy per field).  Fields are concatenated in instance
+   order: instance k occupies the nx_k ny_k values that follow those of
+   instances 0 .. k-1, each in the [ny][nx] layout of lbm_get_fields.
+   lbm_set_density_all_async: fluid at rest with those densities, every
+   instance (resets the step counter).  lbm_get_fields_all_async: rho and v
+   of Eq. (6) of every instance (NULL skips a field); valid after lbm_sync.
+   Buffers hold sum_k nx_k ny_k doubles; host buffers as for the per-instance
+   asynchronous calls. */
+lbm_status lbm_set_density_all_async(lbm_ctx* ctx, const double* rho, int src_is_device);
+lbm_status lbm_get_fields_all_async(lbm_ctx* ctx, double* rho, double* ux, double* uy,
+                                    int dst_is_device);
+
 /* Populations f_alpha(x, t) after streaming and the wall rule (the state
    Eq. (6) is evaluated on), FP64 [9][ny][nx]; FP32 storage is shifted back.
    Solid nodes read 0.  Synchronises. */

@@ -17,7 +17,8 @@ STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
 EXPORTS = ["lbm_default_params", "lbm_create", "lbm_create_batch", "lbm_destroy",
            "lbm_instance_size", "lbm_init_droplet", "lbm_set_density", "lbm_step", "lbm_sync",
            "lbm_time", "lbm_get_fields", "lbm_get_populations", "lbm_diagnostics", "lbm_contact_radius",
-           "lbm_set_density_async", "lbm_get_fields_async",
+           "lbm_set_density_async", "lbm_get_fields_async", "lbm_set_density_all_async",
+           "lbm_get_fields_all_async",
            "lbm_set_gw_field", "lbm_set_launch", "lbm_selftest_wait_timeout",
            "lbm_diagnostics_noalloc", "lbm_adjoint", "lbm_save", "lbm_load", "lbm_autotune",
            "lbm_last_error"]
@@ -88,6 +89,8 @@ def load(path=LIB_PATH):
         "lbm_time": (l, [vp]),
         "lbm_get_fields": (i, [vp, i, vp, vp, vp, i]),
         "lbm_get_fields_async": (i, [vp, i, vp, vp, vp, i]),
+        "lbm_set_density_all_async": (i, [vp, vp, i]),
+        "lbm_get_fields_all_async": (i, [vp, vp, vp, vp, i]),
         "lbm_get_populations": (i, [vp, i, vp, i]),
         "lbm_diagnostics": (i, [vp, i, d, d, d, P(LbmDiag)]),
         "lbm_contact_radius": (i, [vp, i, i, d, d, P(ctypes.c_double)]),

@@ -82,6 +82,10 @@ struct lbm_ctx {
   // one launch with cls[j] as its kernel parameter
   std::vector<PhysDesc> cls;
   std::vector<int> cls_beg, cls_n;
+  // node offsets of the instances in concatenated batch fields: instance k
+  // holds [offs[k], offs[k+1]); d_offs is the device copy
+  std::vector<long long> offs;
+  long long* d_offs = nullptr;
   int* d_err = nullptr;       // [0] latched error bits
   unsigned* d_barrier = nullptr;  // [0] arrival counter, [1] error word of the persistent kernel
   int parity = 0;
@@ -355,6 +359,7 @@ static void free_ctx(lbm_ctx* c) {
   for (auto& I : c->inst) free_inst(I);
   cudaFree(c->d_desc);
   cudaFree(c->d_items);
+  cudaFree(c->d_offs);
   cudaFree(c->d_err);
   cudaFree(c->d_barrier);
   cudaFree(c->d_rho);
@@ -536,6 +541,15 @@ extern "C" lbm_status lbm_create_batch(int count, const lbm_instance_desc* descs
     fill_desc(I, prec, c->d_err);
   }
   if (st == LBM_OK) st = upload_descs(c);
+  if (st == LBM_OK) {
+    c->offs.assign(1, 0);
+    for (auto& I : c->inst) c->offs.push_back(c->offs.back() + (long long)I.nx * I.ny);
+    e = cudaMalloc(&c->d_offs, c->offs.size() * sizeof(long long));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->d_offs, c->offs.data(), c->offs.size() * sizeof(long long),
+                     cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = fail(LBM_ERR_CUDA, "offset table: %s", cudaGetErrorString(e));
+  }
   if (st == LBM_OK) st = build_items(c);
   if (st == LBM_OK) {
     e = cudaStreamSynchronize(c->stream);
@@ -789,6 +803,37 @@ extern "C" lbm_status lbm_contact_radius(lbm_ctx* c, int inst, int row, double l
   CK(launch_contact_scan(c->d_rho, I.nx, level, xi, c->d_rho + I.nx, c->stream));
   CK(cudaMemcpyAsync(r_out, c->d_rho + I.nx, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   return lbm_sync(c);
+}
+
+extern "C" lbm_status lbm_set_density_all_async(lbm_ctx* c, const double* rho,
+                                                int src_is_device) {
+  if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+  if (!rho) return fail(LBM_ERR_ARG, "rho is NULL");
+  const long long total = c->offs.back();
+  lbm_status st = ensure_scratch(c, (size_t)total);
+  if (st != LBM_OK) return st;
+  CK(cudaMemcpyAsync(c->d_rho, rho, total * sizeof(double),
+                     src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  CK(launch_init_all(c->prec, c->d_desc, c->d_offs, (int)c->inst.size(), total, c->parity, c->d_rho,
+                     c->stream));
+  c->t = 0;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_fields_all_async(lbm_ctx* c, double* rho, double* ux, double* uy,
+                                               int dst_is_device) {
+  if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+  const long long total = c->offs.back();
+  lbm_status st = ensure_scratch(c, (size_t)total);
+  if (st != LBM_OK) return st;
+  CK(launch_macro_all(c->prec, c->d_desc, c->d_offs, (int)c->inst.size(), total, c->parity,
+                      c->d_rho, c->d_psi, (ux || uy) ? c->d_ux : nullptr,
+                      (ux || uy) ? c->d_uy : nullptr, c->stream));
+  const cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (rho) CK(cudaMemcpyAsync(rho, c->d_rho, total * sizeof(double), k, c->stream));
+  if (ux) CK(cudaMemcpyAsync(ux, c->d_ux, total * sizeof(double), k, c->stream));
+  if (uy) CK(cudaMemcpyAsync(uy, c->d_uy, total * sizeof(double), k, c->stream));
+  return LBM_OK;
 }
 
 extern "C" lbm_status lbm_get_populations(lbm_ctx* c, int inst, double* f, int dst_is_device) {

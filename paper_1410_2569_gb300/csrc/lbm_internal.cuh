@@ -152,6 +152,13 @@ cudaError_t launch_row_rho(int prec, const InstDesc& h_inst, const InstDesc* d_i
 // contact radius from one row of rho (lbm_diag.cu); writes out[0]
 cudaError_t launch_contact_scan(const double* d_row, int nx, double level, int xi, double* d_out,
                                 cudaStream_t s);
+// the whole batch at once: instance k's nodes are [offs[k], offs[k+1]) of
+// the concatenated fields, total = offs[n]
+cudaError_t launch_init_all(int prec, const InstDesc* d_inst, const long long* d_offs, int n,
+                            long long total, int parity, const double* d_rho0, cudaStream_t s);
+cudaError_t launch_macro_all(int prec, const InstDesc* d_inst, const long long* d_offs, int n,
+                             long long total, int parity, double* d_rho, double* d_psi,
+                             double* d_ux, double* d_uy, cudaStream_t s);
 cudaError_t launch_macro(int prec, const InstDesc& h_inst, const InstDesc* d_inst, int parity,
                          double* d_rho, double* d_psi, double* d_ux, double* d_uy, double* d_f,
                          cudaStream_t s);

@@ -185,6 +185,36 @@ class Lattice:
         out["status"] = st
         return out
 
+    @property
+    def total_nodes(self):
+        return sum(nx * ny for ny, nx in self.shapes)
+
+    def split(self, flat):
+        """Per-instance [ny][nx] views of a field concatenated in instance
+        order (the layout of the *_all calls)."""
+        out, o = [], 0
+        for ny, nx in self.shapes:
+            out.append(flat[o:o + nx * ny].reshape(ny, nx))
+            o += nx * ny
+        return out
+
+    def set_density_all(self, rho_flat):
+        """Every instance at rest with the concatenated densities (FP64,
+        C-contiguous, unchanged until sync()); enqueued only."""
+        assert rho_flat.dtype == np.float64 and rho_flat.flags.c_contiguous
+        assert rho_flat.size == self.total_nodes
+        check(self._L.lbm_set_density_all_async(self._h, rho_flat.ctypes.data, 0))
+
+    def fields_all(self, out):
+        """Enqueue the read-back of rho, ux, uy of every instance into the
+        concatenated FP64 host arrays out["rho"|"ux"|"uy"]; valid after sync()."""
+        for k in ("rho", "ux", "uy"):
+            a = out[k]
+            assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == self.total_nodes
+        check(self._L.lbm_get_fields_all_async(self._h, *[out[k].ctypes.data
+                                                          for k in ("rho", "ux", "uy")], 0))
+        return out
+
     def contact_radius(self, inst=0, row=1, level=0.0, x_ref=None):
         """Spreading radius along node row `row` (lbm_contact_radius); level
         0 means (rho_L + rho_V) / 2."""

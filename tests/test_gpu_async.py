@@ -55,3 +55,26 @@ def test_async_calls_match_sync(cuda, prec):
         for q in ("rho", "ux", "uy"):
             assert np.array_equal(ref[q], outs[k][q]), (k, q)
         assert np.array_equal(a.populations(k), b.populations(k)), k
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_calls_match_per_instance(cuda, prec):
+    specs = _batch(prec)
+    a, b = lbm.Lattice(specs), lbm.Lattice(specs)
+    flat = _pinned((b.total_nodes,))
+    for k, r in enumerate(b.split(flat)):
+        r[:] = _density(specs[k]["nx"], specs[k]["ny"], k)
+    for k in range(len(specs)):
+        a.set_density(b.split(flat)[k].copy(), inst=k)
+    b.set_density_all(flat)
+    b.sync()
+    for lat in (a, b):
+        lat.step(33)
+    out = {q: _pinned((b.total_nodes,)) for q in ("rho", "ux", "uy")}
+    b.fields_all(out)
+    b.sync()
+    for k in range(len(specs)):
+        ref = a.fields(k)
+        for q in ("rho", "ux", "uy"):
+            assert np.array_equal(ref[q], b.split(out[q])[k]), (k, q)
+        assert np.array_equal(a.populations(k), b.populations(k)), k
