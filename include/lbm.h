@@ -56,8 +56,14 @@ typedef enum {
    interaction with phi(x) = psi(x). */
 typedef enum { LBM_FSI_DENSITY = 0, LBM_FSI_PSI = 1, LBM_FSI_MODIFIED = 2 } lbm_fsi;
 
-/* Equation of state: the piecewise-linear EOS of Eq. (15). */
-typedef enum { LBM_EOS_PIECEWISE_LINEAR = 0 } lbm_eos;
+/* Equation of state: the piecewise-linear EOS of Eq. (15) (the paper's), or
+   the Carnahan-Starling EOS p = rho R T (1 + e + e^2 - e^3) / (1 - e)^3 -
+   a rho^2, e = b rho / 4, as an option the paper does not use (its G_w
+   ranges and sigma are those of Eq. (15)).  Either way psi^2 = 2 (p -
+   rho cs^2) / G (Sec. II.B).  With LBM_FP32_SHIFTED the Carnahan-Starling
+   psi^2 is evaluated in FP64 from the compensated density.  lbm_adjoint
+   supports Eq. (15) only. */
+typedef enum { LBM_EOS_PIECEWISE_LINEAR = 0, LBM_EOS_CARNAHAN_STARLING = 1 } lbm_eos;
 
 /* Wall treatment.  LBM_WALL_NEQ_ONNODE: the rule quoted in Sec. III.A for a
    wall below the node (f2 = f4, f5 = f7 - (f1 - f3)/2 - (Fx + Fy)/4,
@@ -101,7 +107,9 @@ typedef enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1, LBM_FP32_SHIFTED_F64 = 2 } lb
 
 typedef struct {
   lbm_eos eos;
-  /* Eq. (15): theta_V, theta_M, theta_L in units of cs^2, then rho_1, rho_2 */
+  /* Eq. (15): theta_V, theta_M, theta_L in units of cs^2, then rho_1, rho_2;
+     Carnahan-Starling: a, b, R, T (all > 0; the density must stay below
+     4 / b) */
   double eos_p[6];
   double G;     /* interaction strength of Eq. (7); psi needs G < 0 */
   double sigma; /* Eq. (9) */

@@ -16,6 +16,7 @@ Q = 9
 FSI = {"density": 0, "psi": 1, "modified": 2}
 WALL = {"neq": 0, "bb": 1}
 GHOST = {"copy": 0, "mirror": 1, "zero": 2, "skip": 3, "mean": 4}
+EOS = {"pl": 0, "cs": 1}
 OMEGA = {"w": 0, "cs2w": 1}
 
 
@@ -28,7 +29,9 @@ class OracleParams(ctypes.Structure):
                 ("tau_q", ctypes.c_double),
                 ("tau_nu_L", ctypes.c_double), ("tau_nu_V", ctypes.c_double),
                 ("rho_L", ctypes.c_double), ("rho_V", ctypes.c_double),
-                ("wall", ctypes.c_int), ("ghost", ctypes.c_int), ("omega", ctypes.c_int)]
+                ("wall", ctypes.c_int), ("ghost", ctypes.c_int), ("omega", ctypes.c_int),
+                ("eos", ctypes.c_int), ("cs_a", ctypes.c_double), ("cs_b", ctypes.c_double),
+                ("cs_R", ctypes.c_double), ("cs_T", ctypes.c_double)]
 
 
 class OracleDiag(ctypes.Structure):
@@ -90,7 +93,7 @@ def paper_params(**over):
     d = dict(kV=0.64, kM=-0.04, kL=1.0, rho_1=1.36, rho_2=481.04, G=-1.0, sigma=0.084,
              tau_rho=1.0, tau_e=1.0 / 0.8, tau_zeta=1.0 / 0.8, tau_j=1.0, tau_q=1.0 / 1.1,
              tau_nu_L=1.1, tau_nu_V=1.1, rho_L=500.0, rho_V=1.0, wall="neq", ghost="copy",
-             omega="w")
+             omega="w", eos="pl", cs_a=1.0, cs_b=4.0, cs_R=1.0, cs_T=0.0)
     d.update(over)
     return d
 
@@ -100,6 +103,10 @@ def to_struct(params):
     p["wall"] = WALL[p["wall"]] if isinstance(p["wall"], str) else p["wall"]
     p["ghost"] = GHOST[p["ghost"]] if isinstance(p["ghost"], str) else p["ghost"]
     p["omega"] = OMEGA[p["omega"]] if isinstance(p["omega"], str) else p["omega"]
+    p.setdefault("eos", "pl")
+    p["eos"] = EOS[p["eos"]] if isinstance(p["eos"], str) else p["eos"]
+    for k, v in (("cs_a", 1.0), ("cs_b", 4.0), ("cs_R", 1.0), ("cs_T", 0.0)):
+        p.setdefault(k, v)
     return OracleParams(**{k: p[k] for k, _ in OracleParams._fields_})
 
 

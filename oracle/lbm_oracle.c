@@ -86,6 +86,12 @@ static inline double* fa(double* f, const oracle_lbm* o, int a) {
 
 /* ---------------- Eq. (15) and the pseudopotential ---------------- */
 double oracle_p_eos(const oracle_params* p, double rho) {
+  if (p->eos == ORC_EOS_CS) {
+    /* Carnahan-Starling: hard-sphere repulsion and van der Waals attraction */
+    const double e = p->cs_b * rho / 4.0;
+    return rho * p->cs_R * p->cs_T * (1.0 + e + e * e - e * e * e) / ((1.0 - e) * (1.0 - e) * (1.0 - e)) -
+           p->cs_a * rho * rho;
+  }
   const double thV = p->kV * cs2, thM = p->kM * cs2, thL = p->kL * cs2;
   if (rho <= p->rho_1) return rho * thV;
   if (rho <= p->rho_2) return p->rho_1 * thV + (rho - p->rho_1) * thM;

@@ -36,6 +36,10 @@ enum { ORC_GHOST_COPY = 0, ORC_GHOST_MIRROR = 1, ORC_GHOST_ZERO = 2, ORC_GHOST_S
    ORC_OMEGA_CS2W: omega_alpha = cs^2 w_alpha (1/9, 1/36), the sentence
    after Eq. (10) read literally. */
 enum { ORC_OMEGA_W = 0, ORC_OMEGA_CS2W = 1 };
+/* Equation of state: the piecewise-linear EOS of Eq. (15), or Carnahan-
+   Starling, p = rho R T (1 + e + e^2 - e^3) / (1 - e)^3 - a rho^2 with
+   e = b rho / 4 (an option: the paper uses Eq. (15) only). */
+enum { ORC_EOS_PL = 0, ORC_EOS_CS = 1 };
 
 typedef struct {
   /* Eq. (15): theta_V, theta_M, theta_L in units of cs^2, spinodal rho_1, rho_2 */
@@ -48,6 +52,8 @@ typedef struct {
      between rho_V and rho_L (clamped) when they differ */
   double tau_nu_L, tau_nu_V, rho_L, rho_V;
   int wall, ghost, omega;
+  int eos;                     /* ORC_EOS_* */
+  double cs_a, cs_b, cs_R, cs_T; /* Carnahan-Starling constants */
 } oracle_params;
 
 typedef struct {

@@ -9,6 +9,7 @@ FSI = {"density": 0, "psi": 1, "modified": 2}
 WALL = {"neq": 0, "bb": 1}
 GHOST = {"copy": 0, "mirror": 1, "zero": 2, "skip": 3, "mean": 4}
 OMEGA = {"w": 0, "cs2w": 1}
+EOS = {"pl": 0, "cs": 1}
 PREC = {"fp64": 0, "fp32": 1, "fp32_f64": 2}
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
           4: "LBM_ERR_NONFINITE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}

@@ -132,10 +132,14 @@ extern "C" lbm_status lbm_default_params(lbm_params* p) {
 
 static lbm_status validate_params(const lbm_params* p) {
   if (!p) return fail(LBM_ERR_ARG, "params is NULL");
-  if (p->eos != LBM_EOS_PIECEWISE_LINEAR) return fail(LBM_ERR_ARG, "unknown EOS %d", (int)p->eos);
+  if (p->eos != LBM_EOS_PIECEWISE_LINEAR && p->eos != LBM_EOS_CARNAHAN_STARLING)
+    return fail(LBM_ERR_ARG, "unknown EOS %d", (int)p->eos);
   if (!(p->G < 0.0)) return fail(LBM_ERR_ARG, "G must be negative for a real psi (got %g)", p->G);
-  if (!(p->eos_p[3] > 0.0 && p->eos_p[4] > p->eos_p[3]))
+  if (p->eos == LBM_EOS_PIECEWISE_LINEAR && !(p->eos_p[3] > 0.0 && p->eos_p[4] > p->eos_p[3]))
     return fail(LBM_ERR_ARG, "need 0 < rho_1 < rho_2");
+  if (p->eos == LBM_EOS_CARNAHAN_STARLING &&
+      !(p->eos_p[0] > 0.0 && p->eos_p[1] > 0.0 && p->eos_p[2] > 0.0 && p->eos_p[3] > 0.0))
+    return fail(LBM_ERR_ARG, "Carnahan-Starling needs a, b, R, T > 0");
   const double taus[] = {p->tau_rho, p->tau_e, p->tau_zeta, p->tau_j, p->tau_q, p->tau_nu_L,
                          p->tau_nu_V};
   for (double t : taus)
@@ -299,6 +303,13 @@ static void fill_desc(Inst& I, int prec, int* d_err) {
   ph.ghost = (int)p.ghost;
   d.var_nu = p.tau_nu_L != p.tau_nu_V;
   ph.omega_cs2w = p.omega == LBM_OMEGA_CS2W;
+  ph.eos = (int)p.eos;
+  if (p.eos == LBM_EOS_CARNAHAN_STARLING) {
+    ph.cs_a = p.eos_p[0];
+    ph.cs_b = p.eos_p[1];
+    ph.cs_RT = p.eos_p[2] * p.eos_p[3];
+    ph.cs_g = 2.0 / (-p.G);
+  }
   d.plane = (long long)I.nx * I.ny;
   d.f[0] = I.f[0];
   d.f[1] = I.f[1];
@@ -1050,6 +1061,8 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, long T, double theta_target, doubl
   if (c->prec != LBM_FP64) return fail(LBM_ERR_ARG, "lbm_adjoint needs LBM_FP64");
   if (c->inst[0].p.ghost == LBM_GHOST_MEAN)
     return fail(LBM_ERR_ARG, "lbm_adjoint supports the COPY, MIRROR, ZERO and SKIP ghosts");
+  if (c->inst[0].p.eos != LBM_EOS_PIECEWISE_LINEAR)
+    return fail(LBM_ERR_ARG, "lbm_adjoint supports the EOS of Eq. (15) only");
   if (T < 1) return fail(LBM_ERR_ARG, "T must be >= 1");
   Inst& I = c->inst[0];
   if (I.p.tau_nu_L != I.p.tau_nu_V)

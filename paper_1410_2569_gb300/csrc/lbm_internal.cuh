@@ -67,7 +67,10 @@ struct Visc {
 struct __align__(16) PhysDesc {
   int wall, ghost;
   int omega_cs2w;  // omega_alpha = cs^2 w_alpha (else w_alpha) in A(x)
-  int pad_;
+  int eos;         // lbm_eos
+  // Carnahan-Starling option: p = rho RT (1 + e + e^2 - e^3) / (1 - e)^3 -
+  // a rho^2, e = b rho / 4; psi^2 = cs_g (rho / 3 - p) with cs_g = 2 / |G|
+  double cs_a, cs_b, cs_RT, cs_g;
   // Eq. (15) as psi^2 = a rho + b per branch (G < 0, c = 1)
   double rho1, rho2, aV, aM, bM, aL, bL;
   // the same as unevaluated FP32 pairs (hi, lo): per branch {a_hi, a_lo,

@@ -7,7 +7,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import FSI, GHOST, OMEGA, PREC, WALL, LbmDiag, LbmInstanceDesc, LbmParams, check
+from ._lib import EOS, FSI, GHOST, OMEGA, PREC, WALL, LbmDiag, LbmInstanceDesc, LbmParams, check
 
 _PARAM_KEYS = ("G", "sigma", "tau_rho", "tau_e", "tau_zeta", "tau_j", "tau_q", "tau_nu_L",
                "tau_nu_V", "rho_L", "rho_V", "rho_ref")
@@ -37,6 +37,11 @@ def to_struct(d):
 
     def enum(v, table):
         return table[v] if isinstance(v, str) else int(v)
+    p.eos = enum(d.get("eos", "pl"), EOS)
+    if p.eos == EOS["cs"]:
+        # Carnahan-Starling: a, b, R, T
+        for j, (k, v) in enumerate((("cs_a", 1.0), ("cs_b", 4.0), ("cs_R", 1.0), ("cs_T", None))):
+            p.eos_p[j] = float(d[k] if k in d or v is None else v)
     p.wall = enum(d.get("wall", "neq"), WALL)
     p.ghost = enum(d.get("ghost", "copy"), GHOST)
     p.omega = enum(d.get("omega", "w"), OMEGA)

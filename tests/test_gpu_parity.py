@@ -63,3 +63,31 @@ def test_rough_surface_bounce_back(cuda, fsi, gw, ghost):
     g = run_gpu(nx, ny, 400, fsi, gwf, solid, drop, wall="bb", ghost=ghost)
     e = field_errors(g, o, solid)
     assert e["rho"] <= 1e-10 and e["f"] <= 1e-10 and e["u"] <= 1e-10, e
+
+
+# Carnahan-Starling option at T = 0.7 T_c (rho_L / rho_V about 38)
+CS = dict(eos="cs", cs_T=0.7 * 0.3773 / 4.0, rho_L=0.358, rho_V=0.0093)
+
+
+@pytest.mark.parametrize("fsi,gw", [("density", 0.05), ("modified", 0.2), ("psi", 0.05)])
+def test_carnahan_starling_fp64_matches_oracle(cuda, fsi, gw):
+    nx, ny, steps = 100, 60, 1000
+    drop = (50.0, 1.0, 20.0, 3.0)
+    solid = inputs.flat_walls(nx, ny)
+    o = run_oracle(nx, ny, steps, fsi, gw, solid, drop, **CS)
+    g = run_gpu(nx, ny, steps, fsi, gw, solid, drop, **CS)
+    assert np.isfinite(o.fields()["rho"]).all()
+    e = field_errors(g, o, solid)
+    assert e["rho"] <= 1e-10 and e["f"] <= 1e-10 and e["u"] <= 1e-10, e
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_f64"])
+def test_carnahan_starling_fp32_density(cuda, prec):
+    nx, ny, steps = 100, 60, 1000
+    drop = (50.0, 1.0, 20.0, 3.0)
+    solid = inputs.flat_walls(nx, ny)
+    o = run_oracle(nx, ny, steps, "modified", 0.2, solid, drop, **CS)
+    g = run_gpu(nx, ny, steps, "modified", 0.2, solid, drop, prec=prec, rho_ref=CS["rho_V"], **CS)
+    fluid = solid == 0
+    ro, rg = o.fields()["rho"][fluid], g.fields()["rho"][fluid]
+    assert np.max(np.abs(rg - ro) / ro) <= 1e-4
