@@ -320,6 +320,14 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int steps, int* bx, int* h, int* stages, d
    when the wait gave up as designed; any other status means it did not. */
 lbm_status lbm_selftest_wait_timeout(void* stream, double seconds);
 
+/* Self-test of the FP32 reciprocal and square root of the FP32 step (a
+   hardware approximation refined by one Newton-Raphson step) against the
+   correctly rounded CUDA ones.  x: n host floats; out: 4 n host floats,
+   out[4 i + 0..3] = step reciprocal, correctly rounded reciprocal, step
+   square root, correctly rounded square root of x[i].  Synchronises the
+   default stream.  LBM_ERR_ARG for NULL pointers or n < 1. */
+lbm_status lbm_selftest_fp32_math(long n, const float* x, float* out);
+
 /* Diagnostics without any device allocation, for callers that cannot call
    cudaMalloc: a host program whose device memory is owned entirely by its
    own allocator or budget, or a time-critical loop that must not pay the

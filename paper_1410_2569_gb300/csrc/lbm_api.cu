@@ -955,6 +955,20 @@ extern "C" lbm_status lbm_selftest_wait_timeout(void* stream, double seconds) {
   return LBM_OK;
 }
 
+extern "C" lbm_status lbm_selftest_fp32_math(long n, const float* x, float* out) {
+  if (!x || !out || n < 1) return fail(LBM_ERR_ARG, "need x, out and n >= 1");
+  float *dx = nullptr, *dout = nullptr;
+  cudaError_t e = cudaMalloc(&dx, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&dout, 4 * n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(dx, x, n * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_math_selftest(dx, dout, n, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, 4 * n * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaFree(dx);
+  cudaFree(dout);
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "math selftest: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // lbm_adjoint: loss L = (theta - theta_target)^2 after T steps and dL/dG_w.
 // ---------------------------------------------------------------------------

@@ -135,6 +135,9 @@ cudaError_t launch_adjoint_step(const InstDesc& h, const InstDesc* d_inst, const
                                 const double* lam_next, double* lam_out, double* grad,
                                 AdjScratch& s, cudaStream_t st);
 
+// FP32 reciprocal / square root self-test (lbm_kernels.cu)
+cudaError_t launch_math_selftest(const float* d_x, float* d_out, long n, cudaStream_t s);
+
 // records the calling thread's lbm_last_error() message and returns s
 lbm_status set_error(lbm_status s, const char* fmt, ...);
 
