@@ -249,24 +249,36 @@ def run_ours(args, ws, rank, local):
         lat = results["fp32"]["lat"]
         n_inst = len(inputs.sweep_cases())
         total = lat.total_nodes
+        chunk, iters = max(1, args.steps // 2), 2
         # pinned host fields of the whole batch, concatenated in instance
-        # order: one upload, one read-back per field, one synchronisation
+        # order: one upload and one read-back per field and iteration; each
+        # iteration's fields land in their own host arrays
         host_rho = torch.empty(total, dtype=torch.float64).pin_memory().numpy()
-        host_out = {k: torch.empty(total, dtype=torch.float64).pin_memory().numpy()
-                    for k in ("rho", "ux", "uy")}
+        host_out = [{k: torch.empty(total, dtype=torch.float64).pin_memory().numpy()
+                     for k in ("rho", "ux", "uy")} for _ in range(iters)]
         one = droplet_density(NX, NY, NX / 2, y_w, R, inputs.SWEEP_WIDTH)
         for v in lat.split(host_rho):
             v[:] = one
-        chunk, iters = max(1, args.steps // 2), 2
+        # one untimed iteration: the library makes its copy streams and the
+        # upload staging buffer on first use
+        lat.set_density_all(host_rho)
+        lat.step(1)
+        lat.fields_all(host_out[0])
+        lat.sync()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(iters):
+        # the library overlaps each upload with the steps queued before it
+        # and each read-back with the steps queued after it; one
+        # synchronisation at the end, inside the timed region
+        for it in range(iters):
             lat.set_density_all(host_rho)
             lat.step(chunk)
-            lat.fields_all(host_out)
-            lat.sync()
+            lat.fields_all(host_out[it])
+        lat.sync()
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
+        for o in host_out:  # every iteration's fields arrived
+            assert np.isfinite(o["rho"]).all() and o["rho"].max() > 100.0
         e2e = {"value": round(ws * nodes * chunk * iters / te / 1e6, 2), "unit": "MLUPS",
                "h2d_bytes_per_step": n_inst * NX * NY * 8 / chunk,
                "d2h_bytes_per_step": 3 * n_inst * NX * NY * 8 / chunk,

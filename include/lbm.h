@@ -200,7 +200,8 @@ lbm_status lbm_set_density_async(lbm_ctx* ctx, int inst, const double* rho, int 
    enqueueing on the context's stream. */
 lbm_status lbm_step(lbm_ctx* ctx, long n);
 
-/* Waits for the context's stream; returns a latched device error if any. */
+/* Waits for the context's stream and for the host copies of the batch
+   calls below; returns a latched device error if any. */
 lbm_status lbm_sync(lbm_ctx* ctx);
 
 long lbm_time(const lbm_ctx* ctx);
@@ -226,8 +227,14 @@ lbm_status lbm_get_fields_async(lbm_ctx* ctx, int inst, double* rho, double* ux,
    lbm_set_density_all_async: fluid at rest with those densities, every
    instance (resets the step counter).  lbm_get_fields_all_async: rho and v
    of Eq. (6) of every instance (NULL skips a field); valid after lbm_sync.
-   Buffers hold sum_k nx_k ny_k doubles; host buffers as for the per-instance
-   asynchronous calls. */
+   Buffers hold sum_k nx_k ny_k doubles.  Device buffers are read or written
+   in the context's stream order (a device density source is read in place).
+   Host buffers go through two copy streams of the context's own, ordered
+   against its stream by events: the upload of host densities into a staging
+   buffer starts at once, beside the steps already queued, and the read-back
+   to the host runs beside the steps queued after it.  A host buffer must
+   stay valid and unchanged (inputs) or unread (outputs) until lbm_sync;
+   page-locked host memory lets the copies run asynchronously. */
 lbm_status lbm_set_density_all_async(lbm_ctx* ctx, const double* rho, int src_is_device);
 lbm_status lbm_get_fields_all_async(lbm_ctx* ctx, double* rho, double* ux, double* uy,
                                     int dst_is_device);

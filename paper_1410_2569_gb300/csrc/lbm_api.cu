@@ -98,6 +98,15 @@ struct lbm_ctx {
   size_t scratch_n = 0;
   double *d_rho = nullptr, *d_psi = nullptr, *d_ux = nullptr, *d_uy = nullptr;
   DiagScratch diag{};
+  // host transfers of the batch calls, on streams of their own so that they
+  // overlap the steps: xs_in copies host densities into d_in, xs_out copies
+  // the scratch fields to the host.  ev_in_free: the last initialisation
+  // has read d_in; ev_out_free: the last read-back has left the scratch.
+  cudaStream_t xs_in = nullptr, xs_out = nullptr;
+  cudaEvent_t ev_in_ready = nullptr, ev_in_free = nullptr;
+  cudaEvent_t ev_out_ready = nullptr, ev_out_free = nullptr;
+  double* d_in = nullptr;
+  size_t in_n = 0;
 };
 
 static size_t tsize(int prec) { return prec == LBM_FP64 ? sizeof(double) : sizeof(float); }
@@ -378,6 +387,17 @@ static void free_ctx(lbm_ctx* c) {
   cudaFree(c->d_ux);
   cudaFree(c->d_uy);
   diag_free(c->diag);
+  if (c->xs_in) {
+    cudaStreamSynchronize(c->xs_in);
+    cudaStreamSynchronize(c->xs_out);
+    cudaStreamDestroy(c->xs_in);
+    cudaStreamDestroy(c->xs_out);
+    cudaEventDestroy(c->ev_in_ready);
+    cudaEventDestroy(c->ev_in_free);
+    cudaEventDestroy(c->ev_out_ready);
+    cudaEventDestroy(c->ev_out_free);
+  }
+  cudaFree(c->d_in);
   delete c;
 }
 
@@ -610,8 +630,12 @@ static lbm_status check_inst(const lbm_ctx* c, int inst) {
   return LBM_OK;
 }
 
+// Every user of the scratch fields enqueues its work on c->stream after the
+// last read-back of them (lbm_get_fields_all_async copies from them on xs_out).
 static lbm_status ensure_scratch(lbm_ctx* c, size_t N) {
+  if (c->xs_out) CK(cudaStreamWaitEvent(c->stream, c->ev_out_free, 0));
   if (c->scratch_n >= N) return LBM_OK;
+  if (c->xs_out) CK(cudaStreamSynchronize(c->xs_out));
   cudaFree(c->d_rho);
   cudaFree(c->d_psi);
   cudaFree(c->d_ux);
@@ -754,6 +778,10 @@ extern "C" long lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
 extern "C" lbm_status lbm_sync(lbm_ctx* c) {
   if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
   CK(cudaStreamSynchronize(c->stream));
+  if (c->xs_in) {
+    CK(cudaStreamSynchronize(c->xs_in));
+    CK(cudaStreamSynchronize(c->xs_out));
+  }
   int h[2] = {0, 0};
   CK(cudaMemcpy(&h[0], c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&h[1], c->d_barrier + 1, sizeof(int), cudaMemcpyDeviceToHost));
@@ -816,17 +844,48 @@ extern "C" lbm_status lbm_contact_radius(lbm_ctx* c, int inst, int row, double l
   return lbm_sync(c);
 }
 
+// the side streams and events of the batch host transfers, made on first use
+static lbm_status ensure_xfer(lbm_ctx* c) {
+  if (c->xs_in) return LBM_OK;
+  CK(cudaStreamCreateWithFlags(&c->xs_in, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&c->xs_out, cudaStreamNonBlocking));
+  cudaEvent_t* ev[4] = {&c->ev_in_ready, &c->ev_in_free, &c->ev_out_ready, &c->ev_out_free};
+  for (cudaEvent_t* e : ev) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  return LBM_OK;
+}
+
 extern "C" lbm_status lbm_set_density_all_async(lbm_ctx* c, const double* rho,
                                                 int src_is_device) {
   if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
   if (!rho) return fail(LBM_ERR_ARG, "rho is NULL");
   const long long total = c->offs.back();
-  lbm_status st = ensure_scratch(c, (size_t)total);
+  if (src_is_device) {
+    // read in place, in stream order
+    CK(launch_init_all(c->prec, c->d_desc, c->d_offs, (int)c->inst.size(), total, c->parity, rho,
+                       c->stream));
+    c->t = 0;
+    return LBM_OK;
+  }
+  lbm_status st = ensure_xfer(c);
   if (st != LBM_OK) return st;
-  CK(cudaMemcpyAsync(c->d_rho, rho, total * sizeof(double),
-                     src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-  CK(launch_init_all(c->prec, c->d_desc, c->d_offs, (int)c->inst.size(), total, c->parity, c->d_rho,
+  if (c->in_n < (size_t)total) {
+    CK(cudaStreamSynchronize(c->xs_in));
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(c->d_in);
+    c->d_in = nullptr;
+    c->in_n = 0;
+    CK(cudaMalloc(&c->d_in, total * sizeof(double)));
+    c->in_n = (size_t)total;
+  }
+  // the upload starts at once, beside the steps still queued on c->stream,
+  // as soon as the previous initialisation has read d_in
+  CK(cudaStreamWaitEvent(c->xs_in, c->ev_in_free, 0));
+  CK(cudaMemcpyAsync(c->d_in, rho, total * sizeof(double), cudaMemcpyHostToDevice, c->xs_in));
+  CK(cudaEventRecord(c->ev_in_ready, c->xs_in));
+  CK(cudaStreamWaitEvent(c->stream, c->ev_in_ready, 0));
+  CK(launch_init_all(c->prec, c->d_desc, c->d_offs, (int)c->inst.size(), total, c->parity, c->d_in,
                      c->stream));
+  CK(cudaEventRecord(c->ev_in_free, c->stream));
   c->t = 0;
   return LBM_OK;
 }
@@ -837,13 +896,29 @@ extern "C" lbm_status lbm_get_fields_all_async(lbm_ctx* c, double* rho, double* 
   const long long total = c->offs.back();
   lbm_status st = ensure_scratch(c, (size_t)total);
   if (st != LBM_OK) return st;
+  // (ensure_scratch has ordered this after the previous read-back)
+  if (!dst_is_device) {
+    st = ensure_xfer(c);
+    if (st != LBM_OK) return st;
+  }
   CK(launch_macro_all(c->prec, c->d_desc, c->d_offs, (int)c->inst.size(), total, c->parity,
                       c->d_rho, c->d_psi, (ux || uy) ? c->d_ux : nullptr,
                       (ux || uy) ? c->d_uy : nullptr, c->stream));
-  const cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (rho) CK(cudaMemcpyAsync(rho, c->d_rho, total * sizeof(double), k, c->stream));
-  if (ux) CK(cudaMemcpyAsync(ux, c->d_ux, total * sizeof(double), k, c->stream));
-  if (uy) CK(cudaMemcpyAsync(uy, c->d_uy, total * sizeof(double), k, c->stream));
+  const size_t bytes = total * sizeof(double);
+  if (dst_is_device) {
+    if (rho) CK(cudaMemcpyAsync(rho, c->d_rho, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (ux) CK(cudaMemcpyAsync(ux, c->d_ux, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (uy) CK(cudaMemcpyAsync(uy, c->d_uy, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    return LBM_OK;
+  }
+  // the copies to the host run on xs_out beside the next steps on c->stream;
+  // the next user of the scratch waits for ev_out_free
+  CK(cudaEventRecord(c->ev_out_ready, c->stream));
+  CK(cudaStreamWaitEvent(c->xs_out, c->ev_out_ready, 0));
+  if (rho) CK(cudaMemcpyAsync(rho, c->d_rho, bytes, cudaMemcpyDeviceToHost, c->xs_out));
+  if (ux) CK(cudaMemcpyAsync(ux, c->d_ux, bytes, cudaMemcpyDeviceToHost, c->xs_out));
+  if (uy) CK(cudaMemcpyAsync(uy, c->d_uy, bytes, cudaMemcpyDeviceToHost, c->xs_out));
+  CK(cudaEventRecord(c->ev_out_free, c->xs_out));
   return LBM_OK;
 }
 

@@ -205,7 +205,15 @@ class Lattice:
 
     def set_density_all(self, rho_flat):
         """Every instance at rest with the concatenated densities (FP64,
-        C-contiguous, unchanged until sync()); enqueued only."""
+        C-contiguous); enqueued only.  A host array must stay unchanged until
+        sync(); a torch CUDA tensor is read in the context's stream order."""
+        if hasattr(rho_flat, "data_ptr") and rho_flat.is_cuda:
+            import torch
+            assert rho_flat.dtype == torch.float64 and rho_flat.is_contiguous()
+            assert rho_flat.numel() == self.total_nodes
+            check(self._L.lbm_set_density_all_async(self._h, ctypes.c_void_p(rho_flat.data_ptr()),
+                                                    1))
+            return
         assert rho_flat.dtype == np.float64 and rho_flat.flags.c_contiguous
         assert rho_flat.size == self.total_nodes
         check(self._L.lbm_set_density_all_async(self._h, rho_flat.ctypes.data, 0))

@@ -78,3 +78,79 @@ def test_batch_calls_match_per_instance(cuda, prec):
         for q in ("rho", "ux", "uy"):
             assert np.array_equal(ref[q], b.split(out[q])[k]), (k, q)
         assert np.array_equal(a.populations(k), b.populations(k)), k
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_pipelined_batch_iterations(cuda, prec):
+    """Uploads, steps and read-backs of several iterations queued back to
+    back with one synchronisation (the copies run on the context's copy
+    streams beside the steps) give what one synchronised iteration at a
+    time gives; each iteration starts from densities of its own."""
+    specs = _batch(prec)
+    a, b = lbm.Lattice(specs), lbm.Lattice(specs)
+    total = b.total_nodes
+    iters = 3
+    rho_in = []
+    for it in range(iters):
+        r = _pinned((total,))
+        for k, v in enumerate(b.split(r)):
+            v[:] = _density(specs[k]["nx"], specs[k]["ny"], k + it)
+        rho_in.append(r)
+    outs = [{q: _pinned((total,)) for q in ("rho", "ux", "uy")} for _ in range(iters)]
+    for it in range(iters):
+        b.set_density_all(rho_in[it])
+        b.step(21 + it)
+        b.fields_all(outs[it])
+    b.sync()
+    for it in range(iters):
+        ref = {q: _pinned((total,)) for q in ("rho", "ux", "uy")}
+        a.set_density_all(rho_in[it])
+        a.sync()
+        a.step(21 + it)
+        a.fields_all(ref)
+        a.sync()
+        for q in ("rho", "ux", "uy"):
+            assert np.array_equal(ref[q], outs[it][q]), (it, q)
+    assert np.array_equal(a.populations(2), b.populations(2))
+
+
+def test_batch_calls_interleaved_with_per_instance_calls(cuda):
+    """A per-instance read-back queued right after a batch read-back reuses
+    the scratch fields only after the batch copies have left them."""
+    specs = _batch("fp32")
+    lat = lbm.Lattice(specs)
+    total = lat.total_nodes
+    flat = _pinned((total,))
+    for k, v in enumerate(lat.split(flat)):
+        v[:] = _density(specs[k]["nx"], specs[k]["ny"], k)
+    lat.set_density_all(flat)
+    lat.step(17)
+    out = {q: _pinned((total,)) for q in ("rho", "ux", "uy")}
+    lat.fields_all(out)
+    one = {q: _pinned((specs[3]["ny"], specs[3]["nx"])) for q in ("rho", "ux", "uy")}
+    lat.fields(3, out=one, sync=False)
+    lat.sync()
+    for k in range(len(specs)):
+        ref = lat.fields(k)
+        for q in ("rho", "ux", "uy"):
+            assert np.array_equal(lat.split(out[q])[k], ref[q]), (k, q)
+    for q in ("rho", "ux", "uy"):
+        assert np.array_equal(lat.split(out[q])[3], one[q]), q
+
+
+def test_batch_density_from_device(cuda):
+    """A device density source is read in place, in stream order."""
+    specs = _batch("fp32")
+    a, b = lbm.Lattice(specs), lbm.Lattice(specs)
+    flat = _pinned((a.total_nodes,))
+    for k, v in enumerate(a.split(flat)):
+        v[:] = _density(specs[k]["nx"], specs[k]["ny"], k)
+    a.set_density_all(flat)
+    dev = torch.from_numpy(flat).cuda()
+    torch.cuda.synchronize()
+    b.set_density_all(dev)
+    for lat in (a, b):
+        lat.step(9)
+        lat.sync()
+    for k in range(len(specs)):
+        assert np.array_equal(a.populations(k), b.populations(k)), k
