@@ -396,11 +396,34 @@ def cpu_baseline(args, budget_s=None):
         steps1 += 5
     one = NX * NY * steps1 / (time.perf_counter() - ts) / 1e6
     oracle.set_threads(cores)
+    # the same oracle, all cores, on the small single lattice (100x60,
+    # psi-based G_w = 1.0, R = 20) and on a 1024x512 slice of the large
+    # lattice's pattern (G_w stripes, 30 droplets): about a second each
+    other = {}
+    slice_s = max(0.5, 0.08 * budget)
+    s1 = inputs.flat_walls(100, 60)
+    o = oracle.Lattice(100, 60, oracle.paper_params(), s1, "psi", inputs.wall_gw(s1, 1.0))
+    o.init_droplet(50.0, y_w, 20.0, 2.0)
+    other["100x60"] = _oracle_rate(o, 100 * 60, slice_s)
+    s5, g5, d5 = inputs.large_striped(1024, 512, 30, seed=0)
+    o = oracle.Lattice(1024, 512, oracle.paper_params(), s5, "modified", g5)
+    o.set_density(inputs.droplet_field(1024, 512, d5, 4.0))
+    other["1024x512 striped slice"] = _oracle_rate(o, 1024 * 512, slice_s)
     return {"value": round(done_nodes / t_used / 1e6, 3), "unit": "MLUPS", "cores": cores,
             "kind": "oracle", "cpu_model": cpu_model(), "value_1thread": round(one, 3),
+            "other_lattices_mlups": other,
             "sample": f"{n_inst} of the 72 sweep lattices (400x200), up to {steps_each} steps "
                       f"each, {t_used:.1f} s of CPU time; one thread: the first lattice, "
                       f"{steps1} steps"}
+
+
+def _oracle_rate(o, nodes, seconds):
+    """MLUPS of oracle lattice o stepped for about `seconds`"""
+    ts, steps = time.perf_counter(), 0
+    while time.perf_counter() - ts < seconds and steps < 2000:
+        o.step(2)
+        steps += 2
+    return round(nodes * steps / (time.perf_counter() - ts) / 1e6, 3)
 
 
 def cpu_model():
