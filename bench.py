@@ -242,6 +242,9 @@ def run_ours(args, ws, rank, local):
                            "ms_per_step": round(dt_l / nsteps * 1e3, 4),
                            "algorithmic_GBps": round(ml * 1e6 * BYTES_PER_NODE[prec] / 1e9 / ws, 1)}
             lat.close()
+    extra = None
+    if args.extra and args.prec == "both" and rank == 0:
+        extra = {"batched_uneven": batched_uneven(stream), "adjoint": adjoint_cost(stream)}
     # end-to-end through the C ABI with host buffers: host density fields in,
     # `chunk` steps, host rho/ux/uy fields out, per e2e iteration
     e2e = None
@@ -346,6 +349,8 @@ def run_ours(args, ws, rank, local):
             large, workload="8192x4096, bottom wall in 64-node G_w stripes -0.1/0.3, "
                             "2000 droplets R 10-40, modified interaction",
             hbm_frac_fp32=round(large["fp32"]["algorithmic_GBps"] / hbm, 4)),
+        "batched_uneven": None if extra is None else extra["batched_uneven"],
+        "adjoint": None if extra is None else extra["adjoint"],
         "gpu_launches": args.steps,
         "clocks": f32["clocks"],
         "cpu_baseline": cpu,
@@ -353,6 +358,78 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+def batched_uneven(stream, steps=1000):
+    """The batched workload: 64 lattices of seeded log-uniform sizes (128x64
+    to 512x256), random interaction and G_w per lattice, droplets of radius
+    ny/4, FP32 storage.  MLUPS (all nodes) over `steps` steps for each launch
+    mode: warp strips one launch per step; the same in a CUDA graph of
+    `steps` launches; block rows in one persistent cooperative launch per
+    `steps` steps captured in a graph; the shape lbm_autotune picks."""
+    import paper_1410_2569_gb300 as lbm
+    from paper_1410_2569_gb300 import inputs
+    cases = inputs.batch_instances(64, seed=0)
+    specs = []
+    for c in cases:
+        solid = inputs.flat_walls(c["nx"], c["ny"])
+        specs.append(dict(nx=c["nx"], ny=c["ny"], params=lbm.default_params(prec="fp32"),
+                          solid=solid, fsi=c["fsi"], gw=inputs.wall_gw(solid, c["gw"])))
+    lat = lbm.Lattice(specs, stream=stream)
+    y_w = inputs.wall_height("copy")
+    for k, c in enumerate(cases):
+        lat.init_droplet(c["nx"] / 2, y_w, c["R"], 2.0, inst=k)
+    nodes = sum(c["nx"] * c["ny"] for c in cases)
+    out = {"instances": len(cases), "nodes": nodes, "steps": steps, "unit": "MLUPS"}
+    modes = (("warp_strips", dict(stages=0)), ("warp_strips_graph", dict(stages=0, graph=True)),
+             ("persistent_graph", dict(stages=1, persistent=True, graph=True)))
+    for name, kw in modes:
+        lat.set_launch(**kw)
+        dt = time_device(lat, stream, steps, steps)  # the warm-up captures the graph
+        out[name] = round(nodes * steps / dt / 1e6, 1)
+    lat.set_launch()
+    t = lat.autotune(steps=20)
+    dt = time_device(lat, stream, steps, steps)
+    out["autotuned"] = round(nodes * steps / dt / 1e6, 1)
+    out["autotuned_shape"] = {k: t[k] for k in ("bx", "h", "stages")}
+    lat.close()
+    return out
+
+
+def adjoint_cost(stream, T=2000):
+    """The differentiation workload: 256x128, droplet of radius 32, modified
+    interaction, a G_w field of 256 wall-node parameters (0.1), FP64; the
+    loss (theta - theta_target)^2 with theta_target 10 deg above the initial
+    angle.  Wall time of lbm_adjoint over T steps (forward with checkpoints,
+    seed, reverse sweep, gradient) against T forward steps alone."""
+    import paper_1410_2569_gb300 as lbm
+    from paper_1410_2569_gb300 import inputs
+    nx, ny = 256, 128
+    solid = inputs.flat_walls(nx, ny)
+    gw = inputs.wall_gw(solid, 0.1)
+
+    def fresh():
+        lat = lbm.Lattice.single(nx, ny, lbm.default_params(prec="fp64"), solid, "modified", gw,
+                                 stream=stream)
+        lat.init_droplet(nx / 2, 0.5, 32.0, 2.0)
+        return lat
+    lat = fresh()
+    target = lat.diagnostics(y_w=0.5, x_ref=nx / 2)["theta_deg"] + 10.0
+    lat.step(T)  # warm-up: module load, graphs of the step
+    lat.sync()
+    lat.close()
+    lat = fresh()
+    dt_fwd = time_device(lat, stream, T, 0)
+    lat.close()
+    lat = fresh()
+    t0 = time.perf_counter()
+    loss, theta, grad = lat.adjoint(T, target, 0.5, nx / 2, 3.0)
+    dt_adj = time.perf_counter() - t0
+    lat.close()
+    assert np.isfinite(grad).all() and np.abs(grad[0]).max() > 0.0
+    return {"lattice": [nx, ny], "steps": T, "forward_ms": round(dt_fwd * 1e3, 2),
+            "adjoint_ms": round(dt_adj * 1e3, 2), "adjoint_over_forward": round(dt_adj / dt_fwd, 2),
+            "parameters": int(np.count_nonzero(gw)), "loss": loss, "theta_deg": theta}
 
 
 def cpu_baseline(args, budget_s=None):
@@ -476,6 +553,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", dest="extra", action="store_false",
+                    help="skip the batched-uneven and adjoint figures")
     ap.add_argument("--no-large", dest="large", action="store_false",
                     help="skip the extra 8192x4096 single-lattice figure")
     ap.add_argument("--prec", default="both", choices=["both", "fp32", "fp64"],

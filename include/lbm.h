@@ -287,7 +287,10 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, long T, double theta_target, double y_w, do
                        double d_min, double* loss_out, double* theta_out, double* grad_gw);
 
 /* Launch shape of lbm_step: bx threads per block along x (a block covers
-   bx - 2 columns), h rows per block (0 = choose automatically),
+   bx - 2 columns), h rows per block or strip segment (0 = choose
+   automatically: balanced segments of at most 32 rows for warp strips, 64
+   for blocks; for warp strips the limit is halved, down to 2 rows, while
+   the whole batch gives fewer strips than two per resident warp),
    persistent = 1 runs all n steps in one cooperative launch with a bounded
    grid barrier between steps, graph = 1 captures the n per-step launches (or
    the one persistent launch) in a CUDA graph, reused for every later call
@@ -318,7 +321,8 @@ lbm_status lbm_load(lbm_ctx* ctx, const char* path);
    keeps the fastest.  The state and the step counter are restored after
    every trial, so the call changes nothing but the launch shape; results do
    not depend on the shape.  Outputs (any may be NULL): the chosen bx, h and
-   stages (as in lbm_set_launch) and its time per step in ms. */
+   stages (as in lbm_set_launch; h = 0 is the automatic height) and its time
+   per step in ms. */
 lbm_status lbm_autotune(lbm_ctx* ctx, int steps, int* bx, int* h, int* stages, double* ms);
 
 /* Self-test of the bounded device-side wait used by the persistent step

@@ -458,18 +458,42 @@ static lbm_status build_items(lbm_ctx* c) {
     return fail(LBM_ERR_ARG, "a persistent launch needs one parameter set across the batch "
                              "(this batch has %d)", (int)c->cls.size());
   }
-  // items of instance k: h-row segments of cols-wide strips
+  // items of instance k: h-row segments of cols-wide strips; without a
+  // height from lbm_set_launch, balanced segments of at most hmax rows
+  auto seg_h = [&](const Inst& I, int hmax) {
+    if (c->h > 0) return c->h;
+    const int nseg = (I.ny + hmax - 1) / hmax;
+    int h = (I.ny + nseg - 1) / nseg;
+    if (two_rows) h += h & 1;  // whole row pairs
+    return h;
+  };
+  // at most 64 rows (32 for warp strips: more, shorter strips balance the
+  // waves better).  Warp strips: while the batch gives fewer than two waves
+  // of strips for the resident warps (16 per SM for every warp-strip kernel
+  // at its register count), halve the segment height, down to 2 rows.
+  // Strips shorter than that cost halo rows but fill the GPU: a single
+  // 256x128 lattice in FP64 runs 7x faster with 2-row segments than with
+  // one 32-row segment per strip; with two or more waves the height does
+  // not matter between 16 and 30 rows.
+  int hmax = warp_mode ? 32 : 64;
+  if (warp_mode && c->h <= 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = 2LL * 16 * std::max(sms, 1);
+    auto count = [&](int hm) {
+      long long n = 0;
+      for (const Inst& I : c->inst) {
+        const int h = seg_h(I, hm);
+        n += (long long)((I.ny + h - 1) / h) * ((I.nx + cols - 1) / cols);
+      }
+      return n;
+    };
+    while (hmax > 2 && count(hmax) < want) hmax = std::max(2, hmax / 2);
+  }
   auto add_items = [&](int k, std::vector<WorkItem>& items) {
     const Inst& I = c->inst[k];
-    int h = c->h;
-    if (h <= 0) {
-      // balanced segments of at most 64 rows (32 for warp strips: more,
-      // shorter strips balance the waves better)
-      const int hmax = warp_mode ? 32 : 64;
-      const int nseg = (I.ny + hmax - 1) / hmax;
-      h = (I.ny + nseg - 1) / nseg;
-      if (two_rows) h += h & 1;  // whole row pairs
-    }
+    const int h = seg_h(I, hmax);
     for (int y0 = 0; y0 < I.ny; y0 += h)
       for (int x0 = 0; x0 < I.nx; x0 += cols) items.push_back({k, x0, y0, std::min(I.ny, y0 + h)});
   };
@@ -1429,8 +1453,9 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, int steps, int* bx_out, int* h_ou
   };
   // warp strips (two rows per lane with FP32 storage: even h), warp strips
   // one row per lane, block rows, TMA block rows
-  std::vector<Cand> cands = {{128, 16, 2}, {128, 24, 2}, {128, 32, 2}, {64, 32, 2},
-                             {256, 32, 2}, {256, 25, 3}, {256, 32, 3}, {128, 32, 3},
+  std::vector<Cand> cands = {{128, 0, 2},  {128, 4, 2},  {128, 8, 2},  {128, 16, 2},
+                             {128, 24, 2}, {128, 32, 2}, {64, 32, 2},  {256, 32, 2},
+                             {256, 0, 3},  {256, 8, 3},  {256, 25, 3}, {256, 32, 3}, {128, 32, 3},
                              {224, 32, 1}, {224, 50, 1}, {416, 50, 1}, {224, 50, 8},
                              {416, 50, 8}};
   const int saved[5] = {c->bx, c->h, c->persistent, c->use_graph, c->stages};
