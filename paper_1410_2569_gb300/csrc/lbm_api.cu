@@ -493,9 +493,27 @@ static lbm_status build_items(lbm_ctx* c) {
   }
   auto add_items = [&](int k, std::vector<WorkItem>& items) {
     const Inst& I = c->inst[k];
-    const int h = seg_h(I, hmax);
-    for (int y0 = 0; y0 < I.ny; y0 += h)
-      for (int x0 = 0; x0 < I.nx; x0 += cols) items.push_back({k, x0, y0, std::min(I.ny, y0 + h)});
+    auto strips = [&](int y0, int y1) {
+      for (int x0 = 0; x0 < I.nx; x0 += cols) items.push_back({k, x0, y0, y1});
+    };
+    if (c->h > 0) {
+      for (int y0 = 0; y0 < I.ny; y0 += c->h) strips(y0, std::min(I.ny, y0 + c->h));
+      return;
+    }
+    // the automatic height: nseg segments with the rows (whole pairs for
+    // two rows per lane) spread evenly, so that no segment is much shorter
+    // than the others (200 rows in pairs: 30,30,28,28,28,28,28 rather than
+    // six of 30 and one of 20)
+    const int g = two_rows ? 2 : 1;
+    const int units = (I.ny + g - 1) / g;
+    const int nseg = (I.ny + seg_h(I, hmax) - 1) / seg_h(I, hmax);
+    int y0 = 0;
+    for (int j = 0; j < nseg && y0 < I.ny; ++j) {
+      const int u = units / nseg + (j < units % nseg ? 1 : 0);
+      const int y1 = std::min(I.ny, y0 + u * g);
+      strips(y0, y1);
+      y0 = y1;
+    }
   };
   std::vector<WorkItem> items;
   for (int j = 0; j < (int)c->cls.size(); ++j) {
