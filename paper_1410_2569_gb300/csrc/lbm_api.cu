@@ -887,12 +887,29 @@ extern "C" lbm_status lbm_contact_radius(lbm_ctx* c, int inst, int row, double l
 }
 
 // the side streams and events of the batch host transfers, made on first use
+// (all or nothing: the context keeps none of them if one cannot be made)
 static lbm_status ensure_xfer(lbm_ctx* c) {
   if (c->xs_in) return LBM_OK;
-  CK(cudaStreamCreateWithFlags(&c->xs_in, cudaStreamNonBlocking));
-  CK(cudaStreamCreateWithFlags(&c->xs_out, cudaStreamNonBlocking));
-  cudaEvent_t* ev[4] = {&c->ev_in_ready, &c->ev_in_free, &c->ev_out_ready, &c->ev_out_free};
-  for (cudaEvent_t* e : ev) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  cudaStream_t st[2] = {nullptr, nullptr};
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+    e = cudaStreamCreateWithFlags(&st[k], cudaStreamNonBlocking);
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    for (cudaStream_t x : st)
+      if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t x : ev)
+      if (x) cudaEventDestroy(x);
+    return fail(LBM_ERR_CUDA, "copy streams: %s", cudaGetErrorString(e));
+  }
+  c->xs_in = st[0];
+  c->xs_out = st[1];
+  c->ev_in_ready = ev[0];
+  c->ev_in_free = ev[1];
+  c->ev_out_ready = ev[2];
+  c->ev_out_free = ev[3];
   return LBM_OK;
 }
 
