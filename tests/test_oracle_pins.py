@@ -1,8 +1,9 @@
 """Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
 
 Each test checks the oracle against something other than itself: numbers
-the paper prints, closed forms, an independently written formulation (BGK
-with Guo forcing in velocity space), exact identities of the method, and
+the paper prints, closed forms, independently written formulations (BGK
+with Guo forcing in velocity space; a brute-force dense-matrix stepper of
+the whole step on small lattices), exact identities of the method, and
 conservation laws.  All run on the CPU in seconds.
 """
 import numpy as np
@@ -408,3 +409,130 @@ def test_circle_fit_recovers_cap_angle(theta):
     # radial edges; the fit error is second order in 1/R
     assert abs(d["theta_deg"] - theta) < 0.05, d
     assert abs(d["radius"] - R) < 0.05
+
+
+# ---------------------------------------------------------------- brute force
+
+OPP = np.array([0, 3, 4, 1, 2, 7, 8, 5, 6])
+
+
+def _brute_force_step(f, p, solid, gw, fsi):
+    """One whole time step written directly from the paper with dense 9x9
+    matrices and np.roll: rho (Eq. 6), p of Eq. (15) and psi =
+    sqrt(2 (p - rho cs^2) / G), psi of solid nodes copied from the fluid node
+    next to them along the wall normal, F_m (Eq. 7) and F_ads (Eqs. 10, 11,
+    14 with omega = w), v (Eq. 6), m = M f with M built from its basis
+    vectors, m* of Eq. (4) with the rates of Eq. (2) (tau_nu linear in rho
+    between rho_V and rho_L, clamped) and S of Eq. (9), f* = M^-1 m*, then
+    the pull of Eq. (5) with, at links from solid nodes, halfway bounce-back
+    (p["wall"] == "bb") or the on-node rule of Sec. III.A (f2, f5, f6 at a
+    wall below, mirrored above, with this step's force F)."""
+    e2 = EX ** 2 + EY ** 2
+    M = np.array([np.ones(9), -4 + 3 * e2, 4 - 10.5 * e2 + 4.5 * e2 ** 2, EX, (3 * e2 - 5) * EX,
+                  EY, (3 * e2 - 5) * EY, EX ** 2 - EY ** 2, EX * EY], dtype=float)
+    fluid = solid == 0
+    rho = np.where(fluid, f.sum(0), 1.0)
+    tV, tM, tL = p["kV"] * CS2, p["kM"] * CS2, p["kL"] * CS2
+    r1, r2, G = p["rho_1"], p["rho_2"], p["G"]
+    pe = np.where(rho <= r1, rho * tV, np.where(rho <= r2, r1 * tV + (rho - r1) * tM,
+                                                r1 * tV + (r2 - r1) * tM + (rho - r2) * tL))
+    psi = np.sqrt(2 * (pe - rho * CS2) / G)
+    above_f, below_f = np.roll(fluid, -1, axis=0), np.roll(fluid, 1, axis=0)
+    psi = np.where(fluid, psi, np.where(above_f, np.roll(psi, -1, axis=0),
+                                        np.where(below_f, np.roll(psi, 1, axis=0), 0.0)))
+    sx, sy, ax, ay = (np.zeros_like(rho) for _ in range(4))
+    for a in range(1, 9):
+        w = 1 / 3 if e2[a] == 1 else 1 / 12
+        at = lambda q: np.roll(q, shift=(-EY[a], -EX[a]), axis=(0, 1))  # q(x + e_a)
+        sx += w * at(psi) * EX[a]
+        sy += w * at(psi) * EY[a]
+        ax += w * at(gw) * at(solid.astype(float)) * EX[a]
+        ay += w * at(gw) * at(solid.astype(float)) * EY[a]
+    Fmx, Fmy = -G * psi * sx, -G * psi * sy
+    X = {"density": rho, "psi": psi, "modified": psi ** 2}[fsi]
+    Fx, Fy = Fmx - X * ax, Fmy - X * ay
+    vx = (np.tensordot(EX, f, 1) + 0.5 * Fx) / rho
+    vy = (np.tensordot(EY, f, 1) + 0.5 * Fy) / rho
+    v2 = vx ** 2 + vy ** 2
+    meq = rho * np.array([np.ones_like(rho), -2 + 3 * v2, 1 - 3 * v2, vx, -vx, vy, -vy,
+                          vx ** 2 - vy ** 2, vx * vy])
+    lo, hi = sorted((p["tau_nu_L"], p["tau_nu_V"]))
+    tnu = np.clip(p["tau_nu_V"] + (rho - p["rho_V"]) / (p["rho_L"] - p["rho_V"]) *
+                  (p["tau_nu_L"] - p["tau_nu_V"]), lo, hi)
+    one = np.ones_like(rho)
+    lam = np.array([one / p["tau_rho"], one / p["tau_e"], one / p["tau_zeta"], one / p["tau_j"],
+                    one / p["tau_q"], one / p["tau_j"], one / p["tau_q"], 1 / tnu, 1 / tnu])
+    vF, Fm2 = vx * Fx + vy * Fy, Fmx ** 2 + Fmy ** 2
+    S = np.array([0 * rho,
+                  6 * vF + 12 * p["sigma"] * Fm2 / (psi ** 2 * (p["tau_e"] - 0.5)),
+                  -6 * vF - 12 * p["sigma"] * Fm2 / (psi ** 2 * (p["tau_zeta"] - 0.5)),
+                  Fx, -Fx, Fy, -Fy, 2 * (vx * Fx - vy * Fy), vx * Fy + vy * Fx])
+    m = np.tensordot(M, f, 1)
+    fs = np.tensordot(np.linalg.inv(M), m - lam * (m - meq) + (1 - lam / 2) * S, 1)
+    out = np.empty_like(f)
+    for a in range(9):
+        from_solid = np.roll(solid, shift=(EY[a], EX[a]), axis=(0, 1)) != 0
+        out[a] = np.where(from_solid, fs[OPP[a]], np.roll(fs[a], shift=(EY[a], EX[a]),
+                                                           axis=(0, 1)))
+    if p["wall"] == "neq":
+        bot = fluid & (np.roll(solid, 1, axis=0) != 0)
+        top = fluid & (np.roll(solid, -1, axis=0) != 0)
+        d13 = out[1] - out[3]
+        out[2] = np.where(bot, out[4], out[2])
+        out[5] = np.where(bot, out[7] - 0.5 * d13 - 0.25 * (Fx + Fy), out[5])
+        out[6] = np.where(bot, out[8] + 0.5 * d13 + 0.25 * (Fx - Fy), out[6])
+        out[4] = np.where(top, out[2], out[4])
+        out[8] = np.where(top, out[6] - 0.5 * d13 - 0.25 * (Fx - Fy), out[8])
+        out[7] = np.where(top, out[5] + 0.5 * d13 + 0.25 * (Fx + Fy), out[7])
+    return np.where(fluid[None], out, 0.0)
+
+
+def _wave(nx, ny):
+    x, y = np.meshgrid(np.arange(nx), np.arange(ny))
+    return np.sin(2 * np.pi * x / nx) * np.cos(2 * np.pi * y / ny)
+
+
+def _drop(nx, ny, x0, y0, R):
+    x, y = np.meshgrid(np.arange(nx), np.arange(ny))
+    return 1 + 0.5 * 499 * (1 - np.tanh(np.hypot(x - x0, y - y0) - R))
+
+
+@pytest.mark.parametrize("case", [
+    # periodic 8 x 8: each EOS branch, the kink at rho_2, a small droplet,
+    # density-dependent viscosity
+    dict(n=(8, 8), rho=lambda: 500 + 10 * _wave(8, 8)),
+    dict(n=(8, 8), rho=lambda: 1 + 0.2 * _wave(8, 8)),
+    dict(n=(8, 8), rho=lambda: 480 + 3 * _wave(8, 8)),
+    dict(n=(8, 8), rho=lambda: _drop(8, 8, 3.5, 3.5, 2.5), over=dict(tau_nu_L=0.6, tau_nu_V=1.5)),
+    # 12 x 10 between walls (solid rows 0 and 9, G_w on the bottom one):
+    # the on-node wall rule for each interaction, halfway bounce-back
+    dict(n=(12, 10), walls=True, fsi="modified", gw=0.1, rho=lambda: _drop(12, 10, 6, 0.5, 4)),
+    dict(n=(12, 10), walls=True, fsi="density", gw=-0.05, rho=lambda: _drop(12, 10, 6, 0.5, 4)),
+    dict(n=(12, 10), walls=True, fsi="psi", gw=0.5, rho=lambda: _drop(12, 10, 6, 0.5, 4)),
+    dict(n=(12, 10), walls=True, fsi="modified", gw=0.1, rho=lambda: _drop(12, 10, 6, 0.5, 4),
+         over=dict(wall="bb")),
+])
+def test_brute_force_stepper_matches_oracle(case):
+    """100 steps of the oracle against the dense-matrix stepper above from the
+    same seeded populations: the whole step, walls included, to 1e-13."""
+    nx, ny = case["n"]
+    p = oracle.paper_params(**case.get("over", {}))
+    if case.get("walls"):
+        solid = inputs.flat_walls(nx, ny)
+        gw = inputs.wall_gw(solid, case["gw"])
+    else:
+        solid = np.zeros((ny, nx), np.uint8)
+        gw = np.zeros((ny, nx))
+    fsi = case.get("fsi", "modified")
+    o = oracle.Lattice(nx, ny, p, solid, fsi, gw)
+    rng = np.random.default_rng(0)
+    f = W[:, None, None] * case["rho"]()[None] * (1 + 0.01 * rng.standard_normal((9, ny, nx)))
+    f = np.where(solid[None] == 0, f, 0.0)
+    o.set_populations(f)
+    for _ in range(100):
+        f = _brute_force_step(f, p, solid, gw, fsi)
+    o.step(100)
+    fluid = solid == 0
+    got = o.populations()[:, fluid]
+    assert np.isfinite(f).all()
+    assert np.abs(got - f[:, fluid]).max() / np.abs(f[:, fluid]).max() < 1e-13
