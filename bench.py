@@ -473,19 +473,24 @@ def cpu_baseline(args, budget_s=None):
         steps1 += 5
     one = NX * NY * steps1 / (time.perf_counter() - ts) / 1e6
     oracle.set_threads(cores)
-    # the same oracle, all cores, on the small single lattice (100x60,
-    # psi-based G_w = 1.0, R = 20) and on a 1024x512 slice of the large
-    # lattice's pattern (G_w stripes, 30 droplets): about a second each
+    # the same oracle, all cores and one thread, on the small single lattice
+    # (100x60, psi-based G_w = 1.0, R = 20) and on a 1024x512 slice of the
+    # large lattice's pattern (G_w stripes, 30 droplets): about a second each
     other = {}
-    slice_s = max(0.5, 0.08 * budget)
+    slice_s = max(0.5, 0.05 * budget)
     s1 = inputs.flat_walls(100, 60)
-    o = oracle.Lattice(100, 60, oracle.paper_params(), s1, "psi", inputs.wall_gw(s1, 1.0))
-    o.init_droplet(50.0, y_w, 20.0, 2.0)
-    other["100x60"] = _oracle_rate(o, 100 * 60, slice_s)
     s5, g5, d5 = inputs.large_striped(1024, 512, 30, seed=0)
-    o = oracle.Lattice(1024, 512, oracle.paper_params(), s5, "modified", g5)
-    o.set_density(inputs.droplet_field(1024, 512, d5, 4.0))
-    other["1024x512 striped slice"] = _oracle_rate(o, 1024 * 512, slice_s)
+    rho5 = inputs.droplet_field(1024, 512, d5, 4.0)
+    for threads, key in ((cores, "cores"), (1, "1thread")):
+        oracle.set_threads(threads)
+        o = oracle.Lattice(100, 60, oracle.paper_params(), s1, "psi", inputs.wall_gw(s1, 1.0))
+        o.init_droplet(50.0, y_w, 20.0, 2.0)
+        other.setdefault("100x60", {})[key] = _oracle_rate(o, 100 * 60, slice_s)
+        o = oracle.Lattice(1024, 512, oracle.paper_params(), s5, "modified", g5)
+        o.set_density(rho5)
+        other.setdefault("1024x512 striped slice", {})[key] = _oracle_rate(o, 1024 * 512,
+                                                                           slice_s)
+    oracle.set_threads(cores)
     return {"value": round(done_nodes / t_used / 1e6, 3), "unit": "MLUPS", "cores": cores,
             "kind": "oracle", "cpu_model": cpu_model(), "value_1thread": round(one, 3),
             "other_lattices_mlups": other,
