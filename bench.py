@@ -365,8 +365,10 @@ def batched_uneven(stream, steps=1000):
     to 512x256), random interaction and G_w per lattice, droplets of radius
     ny/4, FP32 storage.  MLUPS (all nodes) over `steps` steps for each launch
     mode: warp strips one launch per step; the same in a CUDA graph of
-    `steps` launches; block rows in one persistent cooperative launch per
-    `steps` steps captured in a graph; the shape lbm_autotune picks."""
+    `steps` launches; one persistent cooperative launch per `steps` steps
+    captured in a graph, block rows with a grid barrier per step or warp
+    strips (one row per lane) waiting on their neighbours; the shape
+    lbm_autotune picks."""
     import paper_1410_2569_gb300 as lbm
     from paper_1410_2569_gb300 import inputs
     cases = inputs.batch_instances(64, seed=0)
@@ -382,7 +384,8 @@ def batched_uneven(stream, steps=1000):
     nodes = sum(c["nx"] * c["ny"] for c in cases)
     out = {"instances": len(cases), "nodes": nodes, "steps": steps, "unit": "MLUPS"}
     modes = (("warp_strips", dict(stages=0)), ("warp_strips_graph", dict(stages=0, graph=True)),
-             ("persistent_graph", dict(stages=1, persistent=True, graph=True)))
+             ("persistent_graph", dict(stages=1, persistent=True, graph=True)),
+             ("persistent_warp_strips_graph", dict(stages=0, persistent=True, graph=True)))
     for name, kw in modes:
         lat.set_launch(**kw)
         dt = time_device(lat, stream, steps, steps)  # the warm-up captures the graph

@@ -291,12 +291,16 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, long T, double theta_target, double y_w, do
    automatically: balanced segments of at most 32 rows for warp strips, 64
    for blocks; for warp strips the limit is halved, down to 2 rows, while
    the whole batch gives fewer strips than two per resident warp),
-   persistent = 1 runs all n steps in one cooperative launch with a bounded
-   grid barrier between steps, graph = 1 captures the n per-step launches (or
+   persistent = 1 runs all n steps in one cooperative launch: block
+   pipelines with a bounded grid barrier between steps, warp strips one row
+   per lane with no barrier (a strip starts a step once the strips within
+   four nodes of it have finished the previous one; every wait is bounded
+   and a time-out returns LBM_ERR_TIMEOUT at the next synchronising call),
+   graph = 1 captures the n per-step launches (or
    the one persistent launch) in a CUDA graph, reused for every later call
    with the same n.  stages selects the step pipeline: 1 = blocks marching up
    rows with loads prefetched into registers; 2 = independent warps, each
-   marching up a 30-column strip (no block barriers; persistent is ignored),
+   marching up a 30-column strip (no block barriers),
    with FP32 storage two rows at a time on the paired FP32 instructions;
    3 = the same warp strips one row at a time; 8 or 16 = blocks marching up rows with a TMA ring of that many source rows
    in shared memory (FP32 storage, every lattice width a multiple of 4);

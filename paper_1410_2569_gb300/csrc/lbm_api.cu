@@ -88,6 +88,10 @@ struct lbm_ctx {
   long long* d_offs = nullptr;
   int* d_err = nullptr;       // [0] latched error bits
   unsigned* d_barrier = nullptr;  // [0] arrival counter, [1] error word of the persistent kernel
+  // persistent warp strips: the items each item waits for (CSR) and the
+  // per-item count of finished steps
+  int *d_nbr_off = nullptr, *d_nbr = nullptr;
+  unsigned* d_done = nullptr;
   int parity = 0;
   long t = 0;
   int bx = 0, h = 0, persistent = 0, use_graph = 0, stages = 0;
@@ -382,6 +386,9 @@ static void free_ctx(lbm_ctx* c) {
   cudaFree(c->d_offs);
   cudaFree(c->d_err);
   cudaFree(c->d_barrier);
+  cudaFree(c->d_nbr_off);
+  cudaFree(c->d_nbr);
+  cudaFree(c->d_done);
   cudaFree(c->d_rho);
   cudaFree(c->d_psi);
   cudaFree(c->d_ux);
@@ -423,6 +430,9 @@ static lbm_status upload_inst(lbm_ctx* c, Inst& I) {
 
 // work items: bx-wide column strips, h-row segments
 static lbm_status build_items(lbm_ctx* c) {
+  // captured graphs refer to the item buffers rebuilt below
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
   // block rows: a block of bx threads covers bx - 2 columns (its two edge
   // lanes evaluate the halo columns); warp strips: each warp covers 30
   const bool warp_mode = c->stages == 0 || c->stages == 2 || c->stages == 3;
@@ -480,7 +490,9 @@ static lbm_status build_items(lbm_ctx* c) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long want = 2LL * 16 * std::max(sms, 1);
+    const long long slots = 16LL * std::max(sms, 1);
+    int maxny = 0;
+    for (const Inst& I : c->inst) maxny = std::max(maxny, I.ny);
     auto count = [&](int hm) {
       long long n = 0;
       for (const Inst& I : c->inst) {
@@ -489,7 +501,14 @@ static lbm_status build_items(lbm_ctx* c) {
       }
       return n;
     };
-    while (hmax > 2 && count(hmax) < want) hmax = std::max(2, hmax / 2);
+    if (c->persistent) {
+      // one launch for all steps, strips waiting on their neighbours: as
+      // many strips as possible but no more than one per resident warp
+      while (hmax < maxny && count(hmax) > slots) hmax *= 2;
+      while (hmax > 2 && count(hmax / 2) <= slots) hmax /= 2;
+    } else {
+      while (hmax > 2 && count(hmax) < 2 * slots) hmax = std::max(2, hmax / 2);
+    }
   }
   auto add_items = [&](int k, std::vector<WorkItem>& items) {
     const Inst& I = c->inst[k];
@@ -527,6 +546,61 @@ static lbm_status build_items(lbm_ctx* c) {
   CK(cudaMalloc(&c->d_items, items.size() * sizeof(WorkItem)));
   CK(cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
   c->n_items = (int)items.size();
+  cudaFree(c->d_nbr_off);
+  cudaFree(c->d_nbr);
+  cudaFree(c->d_done);
+  c->d_nbr_off = c->d_nbr = nullptr;
+  c->d_done = nullptr;
+  if (c->persistent && warp_mode) {
+    // persistent warp strips: item i waits for the items of its instance
+    // whose nodes lie within RADIUS of its own (periodic in x and y); the
+    // relation is symmetric.  Items of an instance are its segments (outer)
+    // times its strips (inner), instances in order (one parameter class).
+    const int RADIUS = 4;
+    std::vector<int> off(1, 0), nb;
+    auto near = [&](int a0, int a1, int b0, int b1, int n) {
+      // [a0 - R, a1 + R) meets [b0, b1) modulo n
+      const int lo = a0 - RADIUS, hi = a1 + RADIUS;
+      if (hi - lo >= n) return true;
+      for (int sh = -n; sh <= n; sh += n)
+        if (lo < b1 + sh && b0 + sh < hi) return true;
+      return false;
+    };
+    size_t i0 = 0;
+    while (i0 < items.size()) {
+      const int k = items[i0].inst;
+      const Inst& I = c->inst[k];
+      size_t i1 = i0;
+      while (i1 < items.size() && items[i1].inst == k) ++i1;
+      const int nstr = (I.nx + cols - 1) / cols;
+      const int nseg = (int)((i1 - i0) / nstr);
+      auto x1 = [&](int s) { return std::min(I.nx, s * cols + cols); };
+      std::vector<std::vector<int>> sn(nstr), gn(nseg);
+      for (int a = 0; a < nstr; ++a)
+        for (int b = 0; b < nstr; ++b)
+          if (near(a * cols, x1(a), b * cols, x1(b), I.nx)) sn[a].push_back(b);
+      for (int a = 0; a < nseg; ++a) {
+        const WorkItem& ia = items[i0 + (size_t)a * nstr];
+        for (int b = 0; b < nseg; ++b) {
+          const WorkItem& ib = items[i0 + (size_t)b * nstr];
+          if (near(ia.y0, ia.y1, ib.y0, ib.y1, I.ny)) gn[a].push_back(b);
+        }
+      }
+      for (int a = 0; a < nseg; ++a)
+        for (int s = 0; s < nstr; ++s) {
+          for (int b : gn[a])
+            for (int u : sn[s]) nb.push_back((int)i0 + b * nstr + u);
+          off.push_back((int)nb.size());
+        }
+      i0 = i1;
+    }
+    CK(cudaMalloc(&c->d_nbr_off, off.size() * sizeof(int)));
+    CK(cudaMemcpy(c->d_nbr_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&c->d_nbr, std::max<size_t>(nb.size(), 1) * sizeof(int)));
+    if (!nb.empty())
+      CK(cudaMemcpy(c->d_nbr, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&c->d_done, items.size() * sizeof(unsigned)));
+  }
   c->bx_used = bx;
   // TMA pipeline: FP32 storage, every lattice width a multiple of 4
   bool tma_ok = c->prec != LBM_FP64;
@@ -540,8 +614,6 @@ static lbm_status build_items(lbm_ctx* c) {
   while (S >= 8 && tma_smem_bytes(bx, S) > (size_t)optin) S /= 2;
   c->stages_used = warp_mode ? (c->stages == 3 ? PIPE_WARP1 : PIPE_WARP)
                               : ((tma_ok && c->stages != 1 && S >= 8) ? S : 0);
-  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-  c->graphs.clear();
   return LBM_OK;
 }
 
@@ -757,14 +829,25 @@ static cudaError_t launch_one_step(lbm_ctx* c, int parity, cudaStream_t s) {
   return cudaSuccess;
 }
 
+// one cooperative launch for all n steps (one parameter class, checked when
+// the items are built): block rows with a grid barrier per step, or warp
+// strips one row per lane, each waiting only for its neighbours.  The
+// kernel's error word is separate from the context's so that a time-out
+// does not hide behind a stale value.
+static cudaError_t launch_persistent(lbm_ctx* c, long n, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(c->d_barrier + 1, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  if (is_warp_pipe(c->stages_used))
+    return launch_step_dataflow(c->prec, c->cls[0], c->d_desc, c->d_items, c->d_nbr_off,
+                                c->d_nbr, c->n_items, c->parity, n, c->bx_used, c->d_done,
+                                (int*)(c->d_barrier + 1), s);
+  return launch_step_persistent(c->prec, c->cls[0], c->d_desc, c->d_items, c->n_items, c->parity,
+                                n, c->bx_used, c->stages_used, c->d_barrier, s);
+}
+
 static lbm_status enqueue_steps(lbm_ctx* c, long n) {
-  if (c->persistent && !is_warp_pipe(c->stages_used)) {
-    // one cooperative launch for all n steps (one parameter class, checked
-    // when the items are built); the kernel's error word is separate from
-    // the context's so that a time-out does not hide behind a stale value
-    CK(cudaMemsetAsync(c->d_barrier + 1, 0, sizeof(unsigned), c->stream));
-    CK(launch_step_persistent(c->prec, c->cls[0], c->d_desc, c->d_items, c->n_items, c->parity,
-                              n, c->bx_used, c->stages_used, c->d_barrier, c->stream));
+  if (c->persistent) {
+    CK(launch_persistent(c, n, c->stream));
     return LBM_OK;
   }
   for (long k = 0; k < n; ++k) CK(launch_one_step(c, (int)((c->parity + k) & 1), c->stream));
@@ -784,13 +867,8 @@ extern "C" lbm_status lbm_step(lbm_ctx* c, long n) {
       cudaGraph_t g;
       cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        if (c->persistent && !is_warp_pipe(c->stages_used)) {
-          // one persistent launch for all n steps, captured once
-          e = cudaMemsetAsync(c->d_barrier + 1, 0, sizeof(unsigned), cap);
-          if (e == cudaSuccess)
-            e = launch_step_persistent(c->prec, c->cls[0], c->d_desc, c->d_items, c->n_items,
-                                       c->parity, n, c->bx_used, c->stages_used, c->d_barrier,
-                                       cap);
+        if (c->persistent) {
+          e = launch_persistent(c, n, cap);  // one persistent launch for all n steps
         } else {
           for (long k = 0; k < n && e == cudaSuccess; ++k)
             e = launch_one_step(c, (int)((c->parity + k) & 1), cap);

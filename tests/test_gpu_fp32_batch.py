@@ -159,3 +159,23 @@ def test_fp64_warp_strips_bitwise(cuda):
     got = _run_batch(specs, 90, dict(stages=2, bx=96, h=13))
     for i in range(len(specs)):
         assert np.array_equal(got.populations(i), ref.populations(i)), i
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_f64"])
+@pytest.mark.parametrize("ghost,wall", [("copy", "neq"), ("mirror", "neq"), ("mean", "bb")])
+@pytest.mark.parametrize("shape", [dict(h=2), dict(h=3, bx=64), dict()])
+def test_persistent_warp_strips_bitwise(cuda, prec, ghost, wall, shape):
+    """Warp strips in one persistent launch, each strip starting a step when
+    the strips within four nodes of it have finished the previous one, give
+    the populations of one launch per step bit for bit.  Short segments make
+    every strip wait on many neighbours; the mirror ghost reads deepest."""
+    specs = []
+    for fsi, gw, nx, ny in [("density", 0.1, 64, 40), ("psi", -1.0, 130, 48),
+                            ("modified", 0.25, 96, 70), ("modified", -0.1, 33, 20)]:
+        specs.append(dict(nx=nx, ny=ny, params=gpu_params(prec=prec, ghost=ghost, wall=wall),
+                          solid=inputs.flat_walls(nx, ny), fsi=fsi, gw=gw,
+                          drop=(nx / 2, 0.5, ny / 3, 2.0)))
+    ref = _run_batch(specs, 150)
+    got = _run_batch(specs, 150, dict(persistent=True, **shape))
+    for i in range(len(specs)):
+        assert np.array_equal(got.populations(i), ref.populations(i)), (i, prec, ghost, shape)
