@@ -145,7 +145,11 @@ class Lattice:
     def set_launch(self, bx=0, h=0, persistent=False, graph=False, stages=0):
         """Launch shape and pipeline of step() (lbm_set_launch): stages 0/2 warp
         strips (two rows per lane with FP32 storage), 3 warp strips one row per
-        lane, 1 block rows, 8/16 block rows with a TMA ring."""
+        lane, 1 block rows, 8/16 block rows with a TMA ring.  persistent=True
+        runs all steps of a call in one cooperative launch (warp strips one
+        row per lane, each waiting only on its neighbours; block rows with a
+        grid barrier); graph=True replays the launches of a call from a CUDA
+        graph."""
         check(self._L.lbm_set_launch(self._h, int(bx), int(h), int(persistent), int(graph),
                                      int(stages)))
 
