@@ -356,6 +356,7 @@ def run_ours(args, ws, rank, local):
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
+    append_log(args, line)
     if dist:
         dist.destroy_process_group()
 
@@ -549,6 +550,30 @@ def run_reference(args, ws, rank):
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+    append_log(args, line)
+
+
+def append_log(args, line):
+    """--log: append the line with the git commit, the host's core count and
+    the GPU's name to a JSONL file (one record per run)."""
+    if not args.log:
+        return
+    rec = dict(line)
+    try:
+        rec["git_commit"] = subprocess.run(["git", "rev-parse", "HEAD"], cwd=ROOT,
+                                           capture_output=True, text=True,
+                                           timeout=10).stdout.strip() or None
+    except (OSError, subprocess.SubprocessError):
+        rec["git_commit"] = None
+    rec["host_cores"] = os.cpu_count()
+    try:
+        import torch
+        rec["gpu_name"] = torch.cuda.get_device_name(0) if torch.cuda.is_available() else None
+    except Exception:
+        rec["gpu_name"] = None
+    rec["time_utc"] = time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())
+    with open(args.log, "a") as fh:
+        fh.write(json.dumps(rec) + "\n")
 
 
 def main():
@@ -563,6 +588,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", dest="extra", action="store_false",
                     help="skip the batched-uneven and adjoint figures")
+    ap.add_argument("--log", default="",
+                    help="also append the JSON line, with the git commit, host cores and GPU "
+                         "name, to this JSONL file")
     ap.add_argument("--no-large", dest="large", action="store_false",
                     help="skip the extra 8192x4096 single-lattice figure")
     ap.add_argument("--prec", default="both", choices=["both", "fp32", "fp64"],

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbm.h"
 #include "lbm_diag.cuh"
 #include "lbm_internal.cuh"
@@ -114,6 +116,12 @@ struct lbm_ctx {
 };
 
 static size_t tsize(int prec) { return prec == LBM_FP64 ? sizeof(double) : sizeof(float); }
+
+// NVTX range over an entry point (a no-op unless a profiler is attached)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 extern "C" lbm_status lbm_default_params(lbm_params* p) {
   if (!p) return fail(LBM_ERR_ARG, "lbm_default_params: NULL");
@@ -789,6 +797,7 @@ static lbm_status enqueue_set_density(lbm_ctx* c, int inst, const double* rho, i
 }
 
 extern "C" lbm_status lbm_set_density(lbm_ctx* c, int inst, const double* rho, int src_is_device) {
+  Range range_("lbm_set_density");
   lbm_status st = enqueue_set_density(c, inst, rho, src_is_device);
   if (st != LBM_OK) return st;
   CK(cudaStreamSynchronize(c->stream));
@@ -855,6 +864,7 @@ static lbm_status enqueue_steps(lbm_ctx* c, long n) {
 }
 
 extern "C" lbm_status lbm_step(lbm_ctx* c, long n) {
+  Range range_("lbm_step");
   if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
   if (n < 0) return fail(LBM_ERR_ARG, "n must be >= 0");
   if (n == 0) return LBM_OK;
@@ -896,6 +906,7 @@ extern "C" lbm_status lbm_step(lbm_ctx* c, long n) {
 extern "C" long lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
 
 extern "C" lbm_status lbm_sync(lbm_ctx* c) {
+  Range range_("lbm_sync");
   if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
   CK(cudaStreamSynchronize(c->stream));
   if (c->xs_in) {
@@ -934,6 +945,7 @@ static lbm_status enqueue_get_fields(lbm_ctx* c, int inst, double* rho, double* 
 
 extern "C" lbm_status lbm_get_fields(lbm_ctx* c, int inst, double* rho, double* ux, double* uy,
                                      int dst_is_device) {
+  Range range_("lbm_get_fields");
   lbm_status st = enqueue_get_fields(c, inst, rho, ux, uy, dst_is_device);
   if (st != LBM_OK) return st;
   return lbm_sync(c);
@@ -993,6 +1005,7 @@ static lbm_status ensure_xfer(lbm_ctx* c) {
 
 extern "C" lbm_status lbm_set_density_all_async(lbm_ctx* c, const double* rho,
                                                 int src_is_device) {
+  Range range_("lbm_set_density_all_async");
   if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
   if (!rho) return fail(LBM_ERR_ARG, "rho is NULL");
   const long long total = c->offs.back();
@@ -1029,6 +1042,7 @@ extern "C" lbm_status lbm_set_density_all_async(lbm_ctx* c, const double* rho,
 
 extern "C" lbm_status lbm_get_fields_all_async(lbm_ctx* c, double* rho, double* ux, double* uy,
                                                int dst_is_device) {
+  Range range_("lbm_get_fields_all_async");
   if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
   const long long total = c->offs.back();
   lbm_status st = ensure_scratch(c, (size_t)total);
@@ -1120,6 +1134,7 @@ extern "C" lbm_status lbm_set_launch(lbm_ctx* c, int bx, int h, int persistent, 
 
 extern "C" lbm_status lbm_diagnostics(lbm_ctx* c, int inst, double y_w, double x_ref,
                                       double d_min, lbm_diag* out) {
+  Range range_("lbm_diagnostics");
   lbm_status st = check_inst(c, inst);
   if (st != LBM_OK) return st;
   if (!out) return fail(LBM_ERR_ARG, "out is NULL");
@@ -1282,6 +1297,7 @@ struct DevBuf {
 extern "C" lbm_status lbm_adjoint(lbm_ctx* c, long T, double theta_target, double y_w,
                                   double x_ref, double d_min, double* loss_out,
                                   double* theta_out, double* grad_gw) {
+  Range range_("lbm_adjoint");
   if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
   if (c->inst.size() != 1) return fail(LBM_ERR_ARG, "lbm_adjoint needs a single-lattice context");
   if (c->prec != LBM_FP64) return fail(LBM_ERR_ARG, "lbm_adjoint needs LBM_FP64");
@@ -1458,6 +1474,7 @@ const char kMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', '1'};
 }  // namespace
 
 extern "C" lbm_status lbm_save(lbm_ctx* c, const char* path) {
+  Range range_("lbm_save");
   if (!c || !path) return fail(LBM_ERR_ARG, "ctx and path are required");
   lbm_status st = lbm_sync(c);
   if (st != LBM_OK) return st;
@@ -1487,6 +1504,7 @@ extern "C" lbm_status lbm_save(lbm_ctx* c, const char* path) {
 }
 
 extern "C" lbm_status lbm_load(lbm_ctx* c, const char* path) {
+  Range range_("lbm_load");
   if (!c || !path) return fail(LBM_ERR_ARG, "ctx and path are required");
   CK(cudaStreamSynchronize(c->stream));
   FILE* fp = fopen(path, "rb");
@@ -1527,6 +1545,7 @@ extern "C" lbm_status lbm_load(lbm_ctx* c, const char* path) {
 
 extern "C" lbm_status lbm_autotune(lbm_ctx* c, int steps, int* bx_out, int* h_out,
                                    int* stages_out, double* ms_out) {
+  Range range_("lbm_autotune");
   if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
   if (steps < 1) return fail(LBM_ERR_ARG, "steps must be >= 1");
   lbm_status st = lbm_sync(c);
