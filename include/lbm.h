@@ -290,7 +290,9 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, long T, double theta_target, double y_w, do
    bx - 2 columns), h rows per block or strip segment (0 = choose
    automatically: balanced segments of at most 32 rows for warp strips, 64
    for blocks; for warp strips the limit is halved, down to 2 rows, while
-   the whole batch gives fewer strips than two per resident warp),
+   the whole batch gives fewer strips than two per resident warp, and for
+   persistent warp strips it is the height that gives the most strips not
+   exceeding one per resident warp),
    persistent = 1 runs all n steps in one cooperative launch: block
    pipelines with a bounded grid barrier between steps, warp strips one row
    per lane with no barrier (a strip starts a step once the strips within
