@@ -203,8 +203,9 @@ def run_ours(args, ws, rank, local):
         for k in range(len(insts)):
             lat.init_droplet(NX / 2, y_w, R, inputs.SWEEP_WIDTH, inst=k)
         if args.launch:
-            bx, h, pers, graph = (int(v) for v in args.launch.split(","))
-            lat.set_launch(bx, h, pers, graph)
+            v = [int(x) for x in args.launch.split(",")]
+            bx, h, pers, graph = v[:4]
+            lat.set_launch(bx, h, pers, graph, v[4] if len(v) > 4 else 0)
         # warm-up, then the timed region bracketed by barrier + synchronize
         lat.step(args.warmup)
         lat.sync()
@@ -582,7 +583,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--launch", default="", help="bx,h,persistent,graph")
+    ap.add_argument("--launch", default="",
+                    help="bx,h,persistent,graph[,stages] as in lbm_set_launch")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

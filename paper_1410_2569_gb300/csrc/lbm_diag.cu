@@ -166,16 +166,21 @@ __global__ void __launch_bounds__(DIAG_THREADS)
   }
 }
 
-// fixed-order reduction of the block partials (deterministic)
-__global__ void k_diag_final(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
-  const int k = threadIdx.x;
+// fixed-order reduction of the block partials (deterministic for a given
+// number of blocks): warp k reduces quantity k, lane l the partials l,
+// l + 32, ... in order, then the 32 lane results in a fixed shuffle tree
+constexpr int DIAG_FINAL_THREADS = DIAG_W * 32;
+__global__ void __launch_bounds__(DIAG_FINAL_THREADS)
+    k_diag_final(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (k >= DIAG_W) return;
-  double v = part[k];
-  for (int b = 1; b < nblocks; ++b) {
-    const double u = part[b * DIAG_W + k];
-    v = k == 1 || k == 3 ? fmax(v, u) : (k == 2 ? fmin(v, u) : v + u);
-  }
-  out[k] = v;
+  const bool is_max = k == 1 || k == 3, is_min = k == 2;
+  auto op = [&](double a, double b) { return is_max ? fmax(a, b) : (is_min ? fmin(a, b) : a + b); };
+  double v = is_max ? -INFINITY : (is_min ? INFINITY : 0.0);
+  for (int b = lane; b < nblocks; b += 32) v = op(v, part[b * DIAG_W + k]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_down_sync(0xffffffffu, v, o));
+  if (lane == 0) out[k] = v;
 }
 
 static void solve3(const double A[3][3], const double b[3], double x[3]) {
@@ -204,7 +209,7 @@ static cudaError_t diagnostics_into_t(double* part, double* out, double* h, int 
   if (blocks > DIAG_BLOCKS) blocks = DIAG_BLOCKS;
   k_diag<0, MaskT><<<blocks, DIAG_THREADS, 0, s>>>(nx, ny, rho, ux, uy, flags, level, y_w,
                                                    x_ref, d_min, 0.0, 0.0, 0.0, part);
-  k_diag_final<<<1, 32, 0, s>>>(part, blocks, out);
+  k_diag_final<<<1, DIAG_FINAL_THREADS, 0, s>>>(part, blocks, out);
   cudaError_t e = cudaMemcpyAsync(h, out, DIAG_W * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
@@ -230,7 +235,7 @@ static cudaError_t diagnostics_into_t(double* part, double* out, double* h, int 
   r->radius = R;
   k_diag<1, MaskT><<<blocks, DIAG_THREADS, 0, s>>>(nx, ny, rho, ux, uy, flags, level, y_w,
                                                    x_ref, d_min, xc, yc, R, part);
-  k_diag_final<<<1, 32, 0, s>>>(part, blocks, out);
+  k_diag_final<<<1, DIAG_FINAL_THREADS, 0, s>>>(part, blocks, out);
   e = cudaMemcpyAsync(h, out, DIAG_W * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
