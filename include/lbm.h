@@ -345,6 +345,20 @@ lbm_status lbm_selftest_wait_timeout(void* stream, double seconds);
    default stream.  LBM_ERR_ARG for NULL pointers or n < 1. */
 lbm_status lbm_selftest_fp32_math(long n, const float* x, float* out);
 
+/* The dependency lists of the persistent warp strips (lbm_set_launch with
+   persistent = 1), for inspection; host only, no GPU needed.  One nx x ny
+   lattice cut into 30-column strips and h-row segments (segments outer,
+   strips inner): item i covers columns [x0, min(nx, x0 + 30)) and rows
+   [y0, y1), written as items3[3 i .. 3 i + 2] = x0, y0, y1.  Item i starts a
+   step once the items nbr[off[i] .. off[i+1]) have finished the previous
+   one: every item with a node within 4 nodes of one of its own along x and
+   along y, periodic (itself included).  *n_items and *n_nbr receive the
+   counts; with items3, off or nbr NULL only the counts are returned.  cap
+   is the capacity of each of items3, off (n_items + 1) and nbr, in ints;
+   LBM_ERR_ARG if one is too small, for NULL counts, nx or ny < 3, h < 1. */
+lbm_status lbm_strip_neighbours(int nx, int ny, int h, int* n_items, int* items3, int* off,
+                                int* nbr, int cap, int* n_nbr);
+
 /* Diagnostics without any device allocation, for callers that cannot call
    cudaMalloc: a host program whose device memory is owned entirely by its
    own allocator or budget, or a time-critical loop that must not pay the

@@ -436,6 +436,55 @@ static lbm_status upload_inst(lbm_ctx* c, Inst& I) {
   return LBM_OK;
 }
 
+// Dependencies of the persistent warp strips: item i waits for the items of
+// its instance whose nodes lie within STRIP_RADIUS nodes of its own along x
+// and along y (periodic); the relation is symmetric and contains i.  Items
+// of an instance are its segments (outer) times its cols-wide strips
+// (inner), instances in order.  shape holds nx, ny per instance.  CSR out:
+// the neighbours of item i are nb[off[i] .. off[i+1]).
+constexpr int STRIP_RADIUS = 4;
+static void strip_neighbours(const std::vector<WorkItem>& items, const std::vector<int>& shape,
+                             int cols, std::vector<int>& off, std::vector<int>& nb) {
+  off.assign(1, 0);
+  nb.clear();
+  auto near = [](int a0, int a1, int b0, int b1, int n) {
+    // [a0 - R, a1 + R) meets [b0, b1) modulo n
+    const int lo = a0 - STRIP_RADIUS, hi = a1 + STRIP_RADIUS;
+    if (hi - lo >= n) return true;
+    for (int sh = -n; sh <= n; sh += n)
+      if (lo < b1 + sh && b0 + sh < hi) return true;
+    return false;
+  };
+  size_t i0 = 0;
+  while (i0 < items.size()) {
+    const int k = items[i0].inst;
+    const int nx = shape[2 * k], ny = shape[2 * k + 1];
+    size_t i1 = i0;
+    while (i1 < items.size() && items[i1].inst == k) ++i1;
+    const int nstr = (nx + cols - 1) / cols;
+    const int nseg = (int)((i1 - i0) / nstr);
+    auto x1 = [&](int st) { return std::min(nx, st * cols + cols); };
+    std::vector<std::vector<int>> sn(nstr), gn(nseg);
+    for (int a = 0; a < nstr; ++a)
+      for (int b = 0; b < nstr; ++b)
+        if (near(a * cols, x1(a), b * cols, x1(b), nx)) sn[a].push_back(b);
+    for (int a = 0; a < nseg; ++a) {
+      const WorkItem& ia = items[i0 + (size_t)a * nstr];
+      for (int b = 0; b < nseg; ++b) {
+        const WorkItem& ib = items[i0 + (size_t)b * nstr];
+        if (near(ia.y0, ia.y1, ib.y0, ib.y1, ny)) gn[a].push_back(b);
+      }
+    }
+    for (int a = 0; a < nseg; ++a)
+      for (int st = 0; st < nstr; ++st) {
+        for (int b : gn[a])
+          for (int u : sn[st]) nb.push_back((int)i0 + b * nstr + u);
+        off.push_back((int)nb.size());
+      }
+    i0 = i1;
+  }
+}
+
 // work items: bx-wide column strips, h-row segments
 static lbm_status build_items(lbm_ctx* c) {
   // captured graphs refer to the item buffers rebuilt below
@@ -560,48 +609,13 @@ static lbm_status build_items(lbm_ctx* c) {
   c->d_nbr_off = c->d_nbr = nullptr;
   c->d_done = nullptr;
   if (c->persistent && warp_mode) {
-    // persistent warp strips: item i waits for the items of its instance
-    // whose nodes lie within RADIUS of its own (periodic in x and y); the
-    // relation is symmetric.  Items of an instance are its segments (outer)
-    // times its strips (inner), instances in order (one parameter class).
-    const int RADIUS = 4;
-    std::vector<int> off(1, 0), nb;
-    auto near = [&](int a0, int a1, int b0, int b1, int n) {
-      // [a0 - R, a1 + R) meets [b0, b1) modulo n
-      const int lo = a0 - RADIUS, hi = a1 + RADIUS;
-      if (hi - lo >= n) return true;
-      for (int sh = -n; sh <= n; sh += n)
-        if (lo < b1 + sh && b0 + sh < hi) return true;
-      return false;
-    };
-    size_t i0 = 0;
-    while (i0 < items.size()) {
-      const int k = items[i0].inst;
-      const Inst& I = c->inst[k];
-      size_t i1 = i0;
-      while (i1 < items.size() && items[i1].inst == k) ++i1;
-      const int nstr = (I.nx + cols - 1) / cols;
-      const int nseg = (int)((i1 - i0) / nstr);
-      auto x1 = [&](int s) { return std::min(I.nx, s * cols + cols); };
-      std::vector<std::vector<int>> sn(nstr), gn(nseg);
-      for (int a = 0; a < nstr; ++a)
-        for (int b = 0; b < nstr; ++b)
-          if (near(a * cols, x1(a), b * cols, x1(b), I.nx)) sn[a].push_back(b);
-      for (int a = 0; a < nseg; ++a) {
-        const WorkItem& ia = items[i0 + (size_t)a * nstr];
-        for (int b = 0; b < nseg; ++b) {
-          const WorkItem& ib = items[i0 + (size_t)b * nstr];
-          if (near(ia.y0, ia.y1, ib.y0, ib.y1, I.ny)) gn[a].push_back(b);
-        }
-      }
-      for (int a = 0; a < nseg; ++a)
-        for (int s = 0; s < nstr; ++s) {
-          for (int b : gn[a])
-            for (int u : sn[s]) nb.push_back((int)i0 + b * nstr + u);
-          off.push_back((int)nb.size());
-        }
-      i0 = i1;
+    std::vector<int> shape;
+    for (const Inst& I : c->inst) {
+      shape.push_back(I.nx);
+      shape.push_back(I.ny);
     }
+    std::vector<int> off, nb;
+    strip_neighbours(items, shape, cols, off, nb);
     CK(cudaMalloc(&c->d_nbr_off, off.size() * sizeof(int)));
     CK(cudaMemcpy(c->d_nbr_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&c->d_nbr, std::max<size_t>(nb.size(), 1) * sizeof(int)));
@@ -1634,5 +1648,34 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, int steps, int* bx_out, int* h_ou
   if (h_out) *h_out = bestc.h;
   if (stages_out) *stages_out = bestc.stages;
   if (ms_out) *ms_out = best / steps;
+  return LBM_OK;
+}
+
+// The strips of one nx x ny lattice in h-row segments (h > 0) and their
+// dependency lists as the persistent warp strips use them, on the host only.
+extern "C" lbm_status lbm_strip_neighbours(int nx, int ny, int h, int* n_items, int* items3,
+                                           int* off, int* nbr, int cap, int* n_nbr) {
+  if (nx < 3 || ny < 3 || h < 1) return fail(LBM_ERR_ARG, "need nx, ny >= 3 and h >= 1");
+  if (!n_items || !n_nbr) return fail(LBM_ERR_ARG, "n_items and n_nbr must not be NULL");
+  const int cols = 30;  // the columns of one warp strip
+  std::vector<WorkItem> items;
+  for (int y0 = 0; y0 < ny; y0 += h)
+    for (int x0 = 0; x0 < nx; x0 += cols) items.push_back({0, x0, y0, std::min(ny, y0 + h)});
+  std::vector<int> o, nb;
+  strip_neighbours(items, {nx, ny}, cols, o, nb);
+  *n_items = (int)items.size();
+  *n_nbr = (int)nb.size();
+  if (!items3 || !off || !nbr) return LBM_OK;  // sizes only
+  if ((long long)items.size() * 3 > cap || (long long)nb.size() > cap ||
+      (long long)o.size() > cap)
+    return fail(LBM_ERR_ARG, "cap too small: %d items, %d neighbours", (int)items.size(),
+                (int)nb.size());
+  for (size_t i = 0; i < items.size(); ++i) {
+    items3[3 * i] = items[i].x0;
+    items3[3 * i + 1] = items[i].y0;
+    items3[3 * i + 2] = items[i].y1;
+  }
+  for (size_t i = 0; i < o.size(); ++i) off[i] = o[i];
+  for (size_t i = 0; i < nb.size(); ++i) nbr[i] = nb[i];
   return LBM_OK;
 }
