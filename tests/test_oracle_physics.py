@@ -40,26 +40,31 @@ def _printed_angle(fsi, gw):
 # printed Fig. 3 angles are reproduced there; see the design notes)
 PSI_SCALE = 0.75
 
+# (interaction, G_w, droplet centre y0, ghost layer of Eq. (7) at the wall,
+# wall height y_w for the contact angle)
 CASES = {
-    "neutral": ("modified", 0.0, 25.5),
-    "density+": ("density", 0.07, 0.5),
-    "modified+": ("modified", 0.1, 0.5),
-    "modified-": ("modified", -0.1, 0.5),
-    "psi+": ("psi", 1.0 * PSI_SCALE, 0.5),
+    "neutral": ("modified", 0.0, 25.5, "copy", 0.5),
+    "density+": ("density", 0.07, 0.5, "copy", 0.5),
+    "modified+": ("modified", 0.1, 0.5, "copy", 0.5),
+    "modified-": ("modified", -0.1, 0.5, "copy", 0.5),
+    "psi+": ("psi", 1.0 * PSI_SCALE, 0.5, "copy", 0.5),
+    # MIRROR makes the first fluid row the symmetry plane of psi: y_w = 1
+    "neutral-mirror": ("modified", 0.0, 1.0, "mirror", 1.0),
 }
 
 
 def _run_sessile(args):
-    fsi, gw, y0 = args
+    fsi, gw, y0, ghost, y_w = args
     import oracle
     from paper_1410_2569_gb300 import inputs
     oracle.set_threads(1)
     nx, ny = 300, 100
     solid = inputs.flat_walls(nx, ny)
-    o = oracle.Lattice(nx, ny, oracle.paper_params(), solid, fsi, inputs.wall_gw(solid, gw))
+    o = oracle.Lattice(nx, ny, oracle.paper_params(ghost=ghost), solid, fsi,
+                       inputs.wall_gw(solid, gw))
     o.init_droplet(nx / 2, y0, 30.0, 2.0)
     o.step(STEPS)
-    return o.diagnostics(0.5, nx / 2, 3.0)
+    return o.diagnostics(y_w, nx / 2, 3.0)
 
 
 def _run_slab(_):
@@ -137,6 +142,15 @@ def test_neutral_wall_gives_ninety_degrees(runs):
     row = [r for r in _table("paper_table1.txt") if r[0] == "90"][0]
     assert abs(d["rho_min"] - float(row[5])) <= 0.02
     assert abs(d["rho_max"] - float(row[6])) <= 0.5
+
+
+def test_neutral_wall_with_mirror_ghost_gives_ninety_degrees(runs):
+    """G_w = 0 with the MIRROR ghost: psi is symmetric about the first fluid
+    row, so Eq. (7) sees the droplet and its mirror image and the angle is
+    90 deg with y_w on that row (Sec. III.A's analytic value)."""
+    d = runs["sessile"]["neutral-mirror"]
+    assert abs(d["theta_deg"] - 90.0) <= 0.7, d
+    assert d["fit_rms"] < 0.2
 
 
 @pytest.mark.parametrize("key,printed_gw", [("density+", 0.07), ("modified+", 0.1),

@@ -212,6 +212,53 @@ def test_skip_removes_fluid_fluid_force_next_to_wall():
     assert np.abs(fl["Fy"][2]).max() > 1.0  # Eq. (7) still acts one row up
 
 
+@pytest.mark.parametrize("ghost,rows", [("copy", 1), ("mirror", 2), ("zero", None)])
+def test_ghost_psi_and_wall_force_on_flat_walls(ghost, rows):
+    """The ghost psi of Eq. (7) applied at the wall (Sec. III.A), by hand.
+    COPY gives a solid node the psi of the fluid node next to it along the
+    wall normal, MIRROR the psi of the node two rows away (the wall's
+    symmetry plane on the first fluid row), ZERO the value 0.  With psi
+    varying only along y the sum of Eq. (7) is the central difference
+    (psi(y+1) - psi(y-1)) / 2, so on the first fluid row F_m,y =
+    -G psi(1) (psi(2) - psi_ghost) / 2 and F_m,x = 0: zero for MIRROR,
+    -G psi(1) psi(2) / 2 for ZERO.  Every row and column carries a different
+    density, so reading a wrong row or column changes the value."""
+    nx, ny = 10, 12
+    solid = inputs.flat_walls(nx, ny)
+    p = oracle.paper_params(ghost=ghost)
+    y = np.arange(ny)[:, None]
+    rho2d = np.broadcast_to(1.0 + 0.05 * y + 30.0 * (y > 4) * (y < 8), (ny, nx)).copy()
+    o = oracle.Lattice(nx, ny, p, solid, "density", 0.0)
+    o.set_density(rho2d)
+    psi = o.fields()["psi"]
+    # fluid psi: the closed forms of the vapour and middle branches (G = -1)
+    for yy in range(1, ny - 1):
+        r = rho2d[yy, 0]
+        ref = np.sqrt(0.72 * CS2 * r) if r <= 1.36 else np.sqrt(2 * CS2 * (1.04 * r - 0.68 * 1.36))
+        assert np.allclose(psi[yy], ref, rtol=1e-14)
+    if rows is None:
+        assert np.array_equal(psi[0], np.zeros(nx)) and np.array_equal(psi[ny - 1], np.zeros(nx))
+    else:
+        assert np.array_equal(psi[0], psi[rows]), (psi[0], psi[rows])
+        assert np.array_equal(psi[ny - 1], psi[ny - 1 - rows])
+    # a density that varies along x too: the ghost keeps its own column
+    rho_x = rho2d * (1.0 + 0.01 * np.arange(nx)[None, :])
+    o.set_density(rho_x)
+    fl = o.fields()
+    if rows is not None:
+        assert np.array_equal(fl["psi"][0], fl["psi"][rows])
+    o.set_density(rho2d)
+    fl = o.fields()
+    g = {"copy": psi[1], "mirror": psi[2], "zero": 0.0 * psi[1]}[ghost]
+    assert np.allclose(fl["Fy"][1], -p["G"] * psi[1] * (psi[2] - g) / 2, rtol=1e-13, atol=1e-15)
+    g_top = {"copy": psi[ny - 2], "mirror": psi[ny - 3], "zero": 0.0 * psi[1]}[ghost]
+    assert np.allclose(fl["Fy"][ny - 2], -p["G"] * psi[ny - 2] * (g_top - psi[ny - 3]) / 2,
+                       rtol=1e-13, atol=1e-15)
+    assert np.abs(fl["Fx"]).max() < 1e-13
+    if ghost == "mirror":
+        assert np.abs(fl["Fy"][1]).max() == 0.0
+
+
 def test_mean_ghost_is_copy_on_flat_walls():
     """MEAN (a ghost layer for walls of any shape) reduces to the COPY ghost
     of Sec. III.A on flat walls: the same populations, bit for bit."""
@@ -419,8 +466,9 @@ OPP = np.array([0, 3, 4, 1, 2, 7, 8, 5, 6])
 def _brute_force_step(f, p, solid, gw, fsi):
     """One whole time step written directly from the paper with dense 9x9
     matrices and np.roll: rho (Eq. 6), p of Eq. (15) and psi =
-    sqrt(2 (p - rho cs^2) / G), psi of solid nodes copied from the fluid node
-    next to them along the wall normal, F_m (Eq. 7) and F_ads (Eqs. 10, 11,
+    sqrt(2 (p - rho cs^2) / G), the ghost psi of solid nodes (COPY: the fluid
+    node next to them along the wall normal; MIRROR: two rows into the fluid;
+    ZERO: 0), F_m (Eq. 7) and F_ads (Eqs. 10, 11,
     14 with omega = w), v (Eq. 6), m = M f with M built from its basis
     vectors, m* of Eq. (4) with the rates of Eq. (2) (tau_nu linear in rho
     between rho_V and rho_L, clamped) and S of Eq. (9), f* = M^-1 m*, then
@@ -437,9 +485,16 @@ def _brute_force_step(f, p, solid, gw, fsi):
     pe = np.where(rho <= r1, rho * tV, np.where(rho <= r2, r1 * tV + (rho - r1) * tM,
                                                 r1 * tV + (r2 - r1) * tM + (rho - r2) * tL))
     psi = np.sqrt(2 * (pe - rho * CS2) / G)
+    # ghost psi of a solid node with fluid above (below) it: the fluid psi d
+    # rows up (down), d = 1 for COPY and 2 for MIRROR; 0 for ZERO
     above_f, below_f = np.roll(fluid, -1, axis=0), np.roll(fluid, 1, axis=0)
-    psi = np.where(fluid, psi, np.where(above_f, np.roll(psi, -1, axis=0),
-                                        np.where(below_f, np.roll(psi, 1, axis=0), 0.0)))
+    d = {"copy": 1, "mirror": 2}.get(p["ghost"])
+    if d is None:
+        ghost_val = np.zeros_like(psi)
+    else:
+        ghost_val = np.where(above_f, np.roll(psi, -d, axis=0),
+                             np.where(below_f, np.roll(psi, d, axis=0), 0.0))
+    psi = np.where(fluid, psi, ghost_val)
     sx, sy, ax, ay = (np.zeros_like(rho) for _ in range(4))
     for a in range(1, 9):
         w = 1 / 3 if e2[a] == 1 else 1 / 12
@@ -511,10 +566,25 @@ def _drop(nx, ny, x0, y0, R):
     dict(n=(12, 10), walls=True, fsi="psi", gw=0.5, rho=lambda: _drop(12, 10, 6, 0.5, 4)),
     dict(n=(12, 10), walls=True, fsi="modified", gw=0.1, rho=lambda: _drop(12, 10, 6, 0.5, 4),
          over=dict(wall="bb")),
+    # the other ghost layers of Eq. (7) at the wall: MIRROR (psi two rows
+    # into the fluid) with each wall treatment, ZERO on a vapour-side wall
+    dict(n=(12, 10), walls=True, fsi="modified", gw=0.1, rho=lambda: _drop(12, 10, 6, 0.5, 4),
+         over=dict(ghost="mirror")),
+    dict(n=(12, 10), walls=True, fsi="density", gw=-0.05, rho=lambda: _drop(12, 10, 6, 0.5, 4),
+         over=dict(ghost="mirror", wall="bb")),
+    # (ZERO, the rough-wall reading of Sec. III.B, with halfway bounce-back:
+    # it leaves the fluid next to the wall an unbalanced cohesive force of
+    # about psi^2 / 2, under which the on-node rule gives negative
+    # populations within two steps, so these run 40 steps)
+    dict(n=(12, 10), walls=True, fsi="psi", gw=0.5, rho=lambda: _drop(12, 10, 6, 5.0, 2.5),
+         over=dict(ghost="zero", wall="bb"), steps=40),
+    dict(n=(12, 10), walls=True, fsi="modified", gw=-0.1, rho=lambda: _drop(12, 10, 6, 5.0, 2.5),
+         over=dict(ghost="zero", wall="bb"), steps=40),
 ])
 def test_brute_force_stepper_matches_oracle(case):
-    """100 steps of the oracle against the dense-matrix stepper above from the
-    same seeded populations: the whole step, walls included, to 1e-13."""
+    """100 steps (40 with ZERO) of the oracle against the dense-matrix stepper
+    above from the same seeded populations: the whole step, walls included,
+    to 1e-13."""
     nx, ny = case["n"]
     p = oracle.paper_params(**case.get("over", {}))
     if case.get("walls"):
@@ -529,9 +599,10 @@ def test_brute_force_stepper_matches_oracle(case):
     f = W[:, None, None] * case["rho"]()[None] * (1 + 0.01 * rng.standard_normal((9, ny, nx)))
     f = np.where(solid[None] == 0, f, 0.0)
     o.set_populations(f)
-    for _ in range(100):
+    steps = case.get("steps", 100)
+    for _ in range(steps):
         f = _brute_force_step(f, p, solid, gw, fsi)
-    o.step(100)
+    o.step(steps)
     fluid = solid == 0
     got = o.populations()[:, fluid]
     assert np.isfinite(f).all()
