@@ -311,6 +311,14 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, long T, double theta_target, double y_w, do
    (LBM_ERR_ARG otherwise). */
 lbm_status lbm_set_launch(lbm_ctx* ctx, int bx, int h, int persistent, int graph, int stages);
 
+/* The launch shape lbm_step uses now (an implementation detail; the paper
+   has no counterpart): threads per block, and the pipeline as a code: 1 =
+   block rows, 2 = FP32 warp strips two rows per lane, 3 = warp strips one
+   row per lane (FP64 and FP32 with FP64 density, stages 3, and every
+   persistent warp-strip launch), 8 or 16 = block rows with a TMA ring; and
+   the persistent flag as set.  Outputs may be NULL. */
+lbm_status lbm_get_launch(const lbm_ctx* ctx, int* bx, int* pipeline, int* persistent);
+
 /* Writes the state of every lattice (post-collision populations, wall
    forces, step counter) to `path`, with a hash of the lattices, parameters,
    masks and G_w fields.  Synchronises. */

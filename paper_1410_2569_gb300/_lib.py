@@ -20,7 +20,7 @@ EXPORTS = ["lbm_default_params", "lbm_create", "lbm_create_batch", "lbm_destroy"
            "lbm_time", "lbm_get_fields", "lbm_get_populations", "lbm_diagnostics", "lbm_contact_radius",
            "lbm_set_density_async", "lbm_get_fields_async", "lbm_set_density_all_async",
            "lbm_get_fields_all_async", "lbm_selftest_fp32_math", "lbm_strip_neighbours",
-           "lbm_set_gw_field", "lbm_set_launch", "lbm_selftest_wait_timeout",
+           "lbm_set_gw_field", "lbm_set_launch", "lbm_get_launch", "lbm_selftest_wait_timeout",
            "lbm_diagnostics_noalloc", "lbm_adjoint", "lbm_save", "lbm_load", "lbm_autotune",
            "lbm_last_error"]
 
@@ -99,6 +99,7 @@ def load(path=LIB_PATH):
         "lbm_contact_radius": (i, [vp, i, i, d, d, P(ctypes.c_double)]),
         "lbm_set_gw_field": (i, [vp, i, vp]),
         "lbm_set_launch": (i, [vp, i, i, i, i, i]),
+        "lbm_get_launch": (i, [vp, P(i), P(i), P(i)]),
         "lbm_selftest_wait_timeout": (i, [vp, d]),
         "lbm_adjoint": (i, [vp, l, d, d, d, d, P(d), P(d), vp]),
         "lbm_save": (i, [vp, ctypes.c_char_p]),

@@ -1146,6 +1146,19 @@ extern "C" lbm_status lbm_set_launch(lbm_ctx* c, int bx, int h, int persistent, 
   return build_items(c);
 }
 
+extern "C" lbm_status lbm_get_launch(const lbm_ctx* c, int* bx, int* pipeline,
+                                      int* persistent) {
+  if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+  int code = c->stages_used;
+  if (code == PIPE_BLOCK) code = 1;
+  else if (code == PIPE_WARP) code = c->prec == LBM_FP32_SHIFTED ? 2 : 3;
+  if (c->persistent && is_warp_pipe(c->stages_used)) code = 3;  // one row per lane
+  if (bx) *bx = c->bx_used;
+  if (pipeline) *pipeline = code;
+  if (persistent) *persistent = c->persistent;
+  return LBM_OK;
+}
+
 extern "C" lbm_status lbm_diagnostics(lbm_ctx* c, int inst, double y_w, double x_ref,
                                       double d_min, lbm_diag* out) {
   Range range_("lbm_diagnostics");

@@ -153,6 +153,15 @@ class Lattice:
         check(self._L.lbm_set_launch(self._h, int(bx), int(h), int(persistent), int(graph),
                                      int(stages)))
 
+    def launch(self):
+        """The launch shape in use (lbm_get_launch): dict(bx, pipeline,
+        persistent); pipeline 2 is the FP32 warp strips with two rows per
+        lane, 3 the warp strips with one row per lane, 1 the block rows."""
+        bx, pl, pe = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(self._L.lbm_get_launch(self._h, ctypes.byref(bx), ctypes.byref(pl),
+                                          ctypes.byref(pe)))
+        return dict(bx=bx.value, pipeline=pl.value, persistent=bool(pe.value))
+
     def fields(self, inst=0, device=False, out=None, sync=True):
         """rho, ux, uy of instance inst: numpy (host) or torch CUDA tensors
         (device=True); `out` may supply the three host arrays (e.g. pinned).
