@@ -28,9 +28,6 @@ sys.path.insert(0, ROOT)
 NX, NY, R = 400, 200, 50.0
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-# FP64 pipe throughput of this GPU model, measured with a DFMA/DADD probe
-# (504 G FP64 instructions/s; 1.008 TFLOP/s counting an FMA as 2 flops)
-FP64_OPS_PER_S = 504e9
 BYTES_PER_NODE = {"fp32": 72.0, "fp32_f64": 72.0, "fp64": 144.0}
 KERNEL_SRC = os.path.join(ROOT, "paper_1410_2569_gb300", "csrc", "lbm_kernels.cu")
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_sweep.md")
@@ -137,6 +134,17 @@ def dist_env():
     return ws, rank, local
 
 
+def fp64_rate():
+    """FP64 pipe throughput of this GPU, DFMA instructions per second, from
+    the library's probe (lbm_selftest_fp64_rate), measured in this run."""
+    import ctypes
+    import paper_1410_2569_gb300 as lbm
+    v = ctypes.c_double()
+    if lbm.load().lbm_selftest_fp64_rate(ctypes.byref(v)) != 0:
+        return None
+    return v.value
+
+
 def measured_peaks():
     try:
         with open(PEAKS_FILE) as fh:
@@ -196,7 +204,7 @@ def run_ours(args, ws, rank, local):
     nodes = len(inputs.sweep_cases()) * NX * NY
     results = {}
     y_w = inputs.wall_height("copy")
-    precs = ("fp32", "fp64") if args.prec == "both" else (args.prec,)
+    precs = ("fp32", "fp32_f64", "fp64") if args.prec == "both" else (args.prec,)
     for prec in precs:
         insts = sweep_instances(prec, ws, rank)
         lat = lbm.Lattice(insts, stream=stream)
@@ -219,10 +227,10 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         dt = max_over_ranks(dt, dist, "cuda")
         mlups = ws * nodes * args.steps / dt / 1e6
-        # contact angle of one tracked instance after warm-up + timed steps
-        d = lat.diagnostics(inst=11, y_w=y_w, x_ref=NX / 2)
-        results[prec] = dict(dt=dt, mlups=mlups, clocks=clk.summary(), theta=d["theta_deg"],
-                             lat=lat)
+        results[prec] = dict(dt=dt, mlups=mlups, clocks=clk.summary(), lat=lat)
+        if prec != "fp32":
+            lat.close()
+            results[prec].pop("lat")
     # the large single lattice (8192 x 4096, striped wall, 2000 droplets):
     # an extra figure beside the sweep, one lattice far larger than L2
     large = None
@@ -243,6 +251,9 @@ def run_ours(args, ws, rank, local):
                            "ms_per_step": round(dt_l / nsteps * 1e3, 4),
                            "algorithmic_GBps": round(ml * 1e6 * BYTES_PER_NODE[prec] / 1e9 / ws, 1)}
             lat.close()
+    accuracy = None
+    if args.accuracy and args.prec == "both" and rank == 0:
+        accuracy = sweep_accuracy()
     extra = None
     if args.extra and args.prec == "both" and rank == 0:
         extra = {"batched_uneven": batched_uneven(stream), "adjoint": adjoint_cost(stream)}
@@ -297,7 +308,7 @@ def run_ours(args, ws, rank, local):
                               for k, v in results.items()}))
         return
     hbm, peak_kind = measured_peaks()
-    f32, f64 = results["fp32"], results["fp64"]
+    f32, f64, f3264 = results["fp32"], results["fp64"], results["fp32_f64"]
     prof = profile_figures()
 
     def roof(prec, dt, steps):
@@ -311,6 +322,7 @@ def run_ours(args, ws, rank, local):
     # collision ~120)
     fp64_ops_node = prof.get("fp64_pipe_thread_ops_per_node", 140.0)
     fp64_alu = nodes * fp64_ops_node * args.steps / f64["dt"] / 1e9
+    fp64_peak = fp64_rate()  # after the timed regions
     cpu = cpu_baseline(args) if not args.no_cpu else None
     line = {
         "metric": "D2Q9 MLUPS & % HBM roofline, FP32 vs FP64 at <=0.5 deg contact-angle error",
@@ -329,7 +341,11 @@ def run_ours(args, ws, rank, local):
                                "3 interactions x 12 G_w x viscosity ratio {1,10}, R=50",
                    "nodes_per_gpu": nodes, "lattice": [NX, NY], "instances": 72,
                    "l2": "inputs larger than L2 (415 MB FP32 populations), no flush",
-                   "parallelism": f"independent sweeps per GPU x{ws}"},
+                   "parallelism": f"independent sweeps per GPU x{ws}",
+                   "precision": "FP32 populations stored as f - w rho_ref; density and psi "
+                                "from compensated FP32 sums (error-free transformations, "
+                                "FP64-grade, no FP64 instruction); FP64 density and psi "
+                                "instructions: fp32_f64"},
         "roofline": {"bound": "hbm", "achieved": round(ach32, 1), "peak": hbm,
                      "unit": "GB/s", "frac": round(ach32 / hbm, 4),
                      "traffic": prof.get("fp32_dram_bytes_per_launch"),
@@ -338,13 +354,24 @@ def run_ours(args, ws, rank, local):
         "fp64": {"value": round(f64["mlups"], 2), "unit": "MLUPS",
                  "ms_per_step": round(f64["dt"] / args.steps * 1e3, 4),
                  "roofline": {"bound": "alu", "achieved": round(fp64_alu, 1),
-                              "peak": FP64_OPS_PER_S / 1e9, "unit": "G FP64 ops/s",
-                              "frac": round(fp64_alu * 1e9 / FP64_OPS_PER_S, 4),
+                              "peak": None if fp64_peak is None else round(fp64_peak / 1e9, 1),
+                              "unit": "G FP64 ops/s",
+                              "frac": None if fp64_peak is None else
+                              round(fp64_alu * 1e9 / fp64_peak, 4),
+                              "peak_kind": "measured in this run: DFMA probe "
+                                           "(lbm_selftest_fp64_rate)",
                               "fp64_ops_per_node": fp64_ops_node,
+                              "fp64_ops_per_node_source": "ncu profile" if
+                              "fp64_pipe_thread_ops_per_node" in prof else "source count",
                               "hbm_achieved_gbs": round(ach64, 1),
                               "hbm_frac": round(ach64 / hbm, 4)},
                  "clocks": f64["clocks"]},
-        "theta_fp32_vs_fp64_deg": round(abs(f32["theta"] - f64["theta"]), 6),
+        "fp32_f64": {"value": round(f3264["mlups"], 2), "unit": "MLUPS",
+                     "ms_per_step": round(f3264["dt"] / args.steps * 1e3, 4),
+                     "what": "FP32 populations with density and psi in FP64 instructions",
+                     "hbm_frac": round(nodes * BYTES_PER_NODE["fp32_f64"] * args.steps /
+                                       f3264["dt"] / 1e9 / hbm, 4)},
+        "accuracy": accuracy,
         "e2e": e2e,
         "large_lattice": None if large is None else dict(
             large, workload="8192x4096, bottom wall in 64-node G_w stripes -0.1/0.3, "
@@ -360,6 +387,50 @@ def run_ours(args, ws, rank, local):
     append_log(args, line)
     if dist:
         dist.destroy_process_group()
+
+
+def sweep_accuracy(steps=30000):
+    """The metric's accuracy condition on sampled sweep lattices: each
+    interaction at both ends of its G_w range at viscosity ratios 1 and 10
+    (12 lattices), `steps` steps in FP32 (default storage), FP32 with FP64
+    density and psi, and FP64; the largest differences from FP64 over the
+    sample.  Outside the timed region."""
+    import paper_1410_2569_gb300 as lbm
+    from paper_1410_2569_gb300 import inputs
+    cases = [c for c in inputs.sweep_cases()
+             if any(np.isclose(c["gw"], v) for v in inputs.GW_RANGES[c["fsi"]])]
+    solid = inputs.flat_walls(NX, NY)
+    fluid = solid == 0
+    res = {}
+    for prec in ("fp64", "fp32", "fp32_f64"):
+        specs = [dict(nx=NX, ny=NY, params=lbm.default_params(prec=prec, tau_nu_L=c["tau_nu_L"],
+                                                               tau_nu_V=c["tau_nu_V"]),
+                      solid=solid, fsi=c["fsi"], gw=inputs.wall_gw(solid, c["gw"]))
+                 for c in cases]
+        lat = lbm.Lattice(specs)
+        for k in range(len(cases)):
+            lat.init_droplet(NX / 2, 0.5, R, inputs.SWEEP_WIDTH, inst=k)
+        lat.step(steps)
+        lat.sync()
+        res[prec] = [(lat.fields(k)["rho"], lat.diagnostics(inst=k, y_w=0.5, x_ref=NX / 2))
+                     for k in range(len(cases))]
+        lat.close()
+    out = {"steps": steps, "lattices": len(cases),
+           "sample": "each interaction at the lowest and highest G_w of its range, viscosity "
+                     "ratios 1 and 10, 400x200, R=50; differences from the FP64 step"}
+    for prec in ("fp32", "fp32_f64"):
+        th, ext, pt, frac, scale = 0.0, 0.0, 0.0, 0.0, 0.0
+        for (r, d), (r64, d64) in zip(res[prec], res["fp64"]):
+            th = max(th, abs(d["theta_deg"] - d64["theta_deg"]))
+            ext = max(ext, *(abs(d[k] / d64[k] - 1.0) for k in ("rho_max", "rho_min", "mass")))
+            diff = np.abs(r - r64)[fluid]
+            rel = diff / r64[fluid]
+            pt, frac = max(pt, float(rel.max())), max(frac, float(np.mean(rel > 1e-4)))
+            scale = max(scale, float(diff.max()) / 499.0)
+        out[prec] = {"theta_max_abs_diff_deg": th, "rho_extrema_mass_max_rel": ext,
+                     "rho_node_max_rel": pt, "rho_node_frac_above_1e-4": frac,
+                     "rho_node_max_abs_over_range": scale}
+    return out
 
 
 def batched_uneven(stream, steps=1000):
@@ -593,9 +664,11 @@ def main():
     ap.add_argument("--log", default="",
                     help="also append the JSON line, with the git commit, host cores and GPU "
                          "name, to this JSONL file")
+    ap.add_argument("--no-accuracy", dest="accuracy", action="store_false",
+                    help="skip the 30,000-step FP32-vs-FP64 accuracy sample")
     ap.add_argument("--no-large", dest="large", action="store_false",
                     help="skip the extra 8192x4096 single-lattice figure")
-    ap.add_argument("--prec", default="both", choices=["both", "fp32", "fp64"],
+    ap.add_argument("--prec", default="both", choices=["both", "fp32", "fp32_f64", "fp64"],
                     help="a single precision prints only its timings (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -353,6 +353,15 @@ lbm_status lbm_selftest_wait_timeout(void* stream, double seconds);
    default stream.  LBM_ERR_ARG for NULL pointers or n < 1. */
 lbm_status lbm_selftest_fp32_math(long n, const float* x, float* out);
 
+/* Throughput of the FP64 pipe of the current device (an implementation
+   detail; the paper has no counterpart): a probe kernel of eight
+   independent chains of dependent FMAs per thread, 8 blocks of 256 threads
+   per SM, timed with CUDA events on its second launch; *ops_per_s receives
+   the DFMA instructions per second.  The FP64 step's roofline is reported
+   against it.  Synchronises the device's default stream; LBM_ERR_ARG for a
+   NULL pointer, LBM_ERR_CUDA if the probe cannot run. */
+lbm_status lbm_selftest_fp64_rate(double* ops_per_s);
+
 /* The dependency lists of the persistent warp strips (lbm_set_launch with
    persistent = 1), for inspection; host only, no GPU needed.  One nx x ny
    lattice cut into 30-column strips and h-row segments (segments outer,

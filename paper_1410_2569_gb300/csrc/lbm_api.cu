@@ -1223,6 +1223,13 @@ extern "C" lbm_status lbm_selftest_fp32_math(long n, const float* x, float* out)
   return LBM_OK;
 }
 
+extern "C" lbm_status lbm_selftest_fp64_rate(double* ops_per_s) {
+  if (!ops_per_s) return fail(LBM_ERR_ARG, "ops_per_s is NULL");
+  cudaError_t e = measure_fp64_rate(ops_per_s);
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "fp64 probe: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // lbm_adjoint: loss L = (theta - theta_target)^2 after T steps and dL/dG_w.
 // ---------------------------------------------------------------------------

@@ -135,6 +135,10 @@ cudaError_t launch_adjoint_step(const InstDesc& h, const InstDesc* d_inst, const
                                 const double* lam_next, double* lam_out, double* grad,
                                 AdjScratch& s, cudaStream_t st);
 
+// FP64 pipe throughput of the current device, DFMA instructions per second
+// (lbm_kernels.cu)
+cudaError_t measure_fp64_rate(double* ops_per_s);
+
 // FP32 reciprocal / square root self-test (lbm_kernels.cu)
 cudaError_t launch_math_selftest(const float* d_x, float* d_out, long n, cudaStream_t s);
 
