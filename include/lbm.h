@@ -353,6 +353,13 @@ lbm_status lbm_selftest_wait_timeout(void* stream, double seconds);
    default stream.  LBM_ERR_ARG for NULL pointers or n < 1. */
 lbm_status lbm_selftest_fp32_math(long n, const float* x, float* out);
 
+/* Self-test of the FP64 reciprocal of the FP64 step (the hardware
+   approximation refined by two Newton-Raphson steps): for n values x (host
+   array), out[2 i], out[2 i + 1] = step reciprocal, correctly rounded
+   reciprocal of x[i].  Synchronises the default stream.  LBM_ERR_ARG for
+   NULL pointers or n < 1. */
+lbm_status lbm_selftest_fp64_math(long n, const double* x, double* out);
+
 /* Throughput of the FP64 pipe of the current device (an implementation
    detail; the paper has no counterpart): a probe kernel of eight
    independent chains of dependent FMAs per thread, 8 blocks of 256 threads
@@ -376,6 +383,19 @@ lbm_status lbm_selftest_fp64_rate(double* ops_per_s);
 lbm_status lbm_strip_neighbours(int nx, int ny, int h, int* n_items, int* items3, int* off,
                                 int* nbr, int cap, int* n_nbr);
 
+/* The work items of a context's lbm_step as built now (an implementation
+   detail; the paper has no counterpart), for inspection: item i is the
+   column strip [x0, x0 + width) of instance inst over rows [y0, y1), written
+   as items4[4 i .. 4 i + 3] = inst, x0, y0, y1.  With persistent warp strips
+   (lbm_set_launch persistent = 1) nbr[off[i] .. off[i+1]) lists the items
+   item i waits for between steps, by the rule of lbm_strip_neighbours;
+   otherwise every list is empty.  *n_items and *n_nbr receive the counts;
+   with items4, off or nbr NULL only the counts are returned.  cap is the
+   capacity of each of items4, off (n_items + 1) and nbr, in ints; LBM_ERR_ARG
+   if one is too small or a count pointer is NULL. */
+lbm_status lbm_get_work_items(const lbm_ctx* ctx, int* n_items, int* items4, int* off, int* nbr,
+                              int cap, int* n_nbr);
+
 /* Diagnostics without any device allocation, for callers that cannot call
    cudaMalloc: a host program whose device memory is owned entirely by its
    own allocator or budget, or a time-critical loop that must not pay the
@@ -390,7 +410,8 @@ lbm_status lbm_strip_neighbours(int nx, int ny, int h, int* n_items, int* items3
    Scratch: a fixed 77,952-byte device array inside the library, kept by
    every GPU that loads it until the process exits.  The first call on a
    device looks up that array's device address (cudaGetSymbolAddress) with
-   the device current; make that first call before any stream capture.  All
+   the device current.  Every call copies its result to the host and
+   synchronises `stream`, so no call can be part of a stream capture.  All
    calls share the array: calls whose work overlaps on a GPU (other streams
    or threads) race and must be serialised by the caller; each call
    overwrites all the scratch it reads, so nothing carries over.

@@ -19,8 +19,9 @@ EXPORTS = ["lbm_default_params", "lbm_create", "lbm_create_batch", "lbm_destroy"
            "lbm_instance_size", "lbm_init_droplet", "lbm_set_density", "lbm_step", "lbm_sync",
            "lbm_time", "lbm_get_fields", "lbm_get_populations", "lbm_diagnostics", "lbm_contact_radius",
            "lbm_set_density_async", "lbm_get_fields_async", "lbm_set_density_all_async",
-           "lbm_get_fields_all_async", "lbm_selftest_fp32_math", "lbm_selftest_fp64_rate",
-           "lbm_strip_neighbours",
+           "lbm_get_fields_all_async", "lbm_selftest_fp32_math", "lbm_selftest_fp64_math",
+           "lbm_selftest_fp64_rate",
+           "lbm_strip_neighbours", "lbm_get_work_items",
            "lbm_set_gw_field", "lbm_set_launch", "lbm_get_launch", "lbm_selftest_wait_timeout",
            "lbm_diagnostics_noalloc", "lbm_adjoint", "lbm_save", "lbm_load", "lbm_autotune",
            "lbm_last_error"]
@@ -94,8 +95,10 @@ def load(path=LIB_PATH):
         "lbm_set_density_all_async": (i, [vp, vp, i]),
         "lbm_get_fields_all_async": (i, [vp, vp, vp, vp, i]),
         "lbm_selftest_fp32_math": (i, [ctypes.c_long, vp, vp]),
+        "lbm_selftest_fp64_math": (i, [ctypes.c_long, vp, vp]),
         "lbm_selftest_fp64_rate": (i, [P(d)]),
         "lbm_strip_neighbours": (i, [i, i, i, P(i), vp, vp, vp, i, P(i)]),
+        "lbm_get_work_items": (i, [vp, P(i), vp, vp, vp, i, P(i)]),
         "lbm_get_populations": (i, [vp, i, vp, i]),
         "lbm_diagnostics": (i, [vp, i, d, d, d, P(LbmDiag)]),
         "lbm_contact_radius": (i, [vp, i, i, d, d, P(ctypes.c_double)]),

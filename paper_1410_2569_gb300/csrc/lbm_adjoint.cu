@@ -9,14 +9,17 @@
 //   f'(x + e_a) = f*_a(x) (Eq. 5), then the wall rule / bounce-back gives
 //   f(t+1).
 // Given lam(t+1) = dL/df(t+1), one reverse step gives lam(t) = dL/df(t) and
-// adds dL/dG_w(z) for every solid node z, in four passes:
-//   k_adj_fields  rho, psi, dpsi/drho on the forward state f(t)
-//   k_adj_walls   adjoint of the wall rule at NEQ wall nodes: lam' and the
+// adds dL/dG_w(z) for every solid node z, in three passes over the forward
+// state f(t) and its rho and psi on fluid nodes, which the recomputation of
+// the forward steps stores beside f(t):
+//   k_adj_walls   ghost psi of the solid nodes; adjoint of the wall rule at
+//                 NEQ wall nodes: lam' and the
 //                 adjoint of the node's force that the rule used
 //   k_adj_node    per fluid node: adjoint of streaming (gather of lam'),
 //                 of the collision and of the local parts of the force
 //   k_adj_gather  per node: transposed psi stencil, ghost sources, d psi /
-//                 d rho, lam(t); on solid nodes the G_w gradient through A.
+//                 d rho (from rho and psi), lam(t); on solid nodes the G_w
+//                 gradient through A.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -71,29 +74,6 @@ __device__ __forceinline__ double psi2_and_slope(const InstDesc& I, double rho, 
 
 }  // namespace
 
-// rho, psi and d psi / d rho of the forward state; ghost psi on solid nodes
-__global__ void k_adj_fields(const InstDesc* __restrict__ insts, const double* __restrict__ f,
-                             double* rho, double* psi, double* dpsi) {
-  const InstDesc& I = insts[0];
-  Node n;
-  if (!node_of(I, n)) return;
-  const long long N = I.plane;
-  const uint16_t fl = I.flags[n.i];
-  if (fl & NF_SELF_SOLID) {
-    rho[n.i] = 0.0;
-    dpsi[n.i] = 0.0;
-    return;  // psi of solid nodes: k_adj_ghost
-  }
-  double r = 0.0;
-  for (int a = 0; a < Q; ++a) r += f[a * N + n.i];
-  double slope;
-  const double p2 = psi2_and_slope(I, r, slope);
-  const double p = sqrt(p2);
-  rho[n.i] = r;
-  psi[n.i] = p;
-  dpsi[n.i] = slope / (2.0 * p);
-}
-
 __device__ __forceinline__ int ghost_offset(const InstDesc& I, uint16_t fl) {
   if (I.ph.ghost != LBM_GHOST_COPY && I.ph.ghost != LBM_GHOST_MIRROR) return 0;
   const int d = I.ph.ghost == LBM_GHOST_COPY ? 1 : 2;
@@ -102,23 +82,21 @@ __device__ __forceinline__ int ghost_offset(const InstDesc& I, uint16_t fl) {
   return 0;
 }
 
-__global__ void k_adj_ghost(const InstDesc* __restrict__ insts, double* psi) {
-  const InstDesc& I = insts[0];
-  Node n;
-  if (!node_of(I, n)) return;
-  const uint16_t fl = I.flags[n.i];
-  if (!(fl & NF_SELF_SOLID)) return;
-  const int d = ghost_offset(I, fl);
-  psi[n.i] = d ? psi[nb(I, n, 0, d)] : 0.0;
-}
-
 // adjoint of the NEQ wall rule (Sec. III.A) at wall nodes; elsewhere lam' = lam
+// (and the ghost psi of solid nodes from the fluid psi of the forward state)
 __global__ void k_adj_walls(const InstDesc* __restrict__ insts, const double* __restrict__ lam,
-                            double* lamp, double2* lamF_bc) {
+                            double* lamp, double2* lamF_bc, double* psi) {
   const InstDesc& I = insts[0];
   Node n;
   if (!node_of(I, n)) return;
   const long long N = I.plane;
+  {
+    const uint16_t fs = I.flags[n.i];
+    if (fs & NF_SELF_SOLID) {
+      const int d = ghost_offset(I, fs);
+      psi[n.i] = d ? psi[nb(I, n, 0, d)] : 0.0;
+    }
+  }
   double l[Q];
   for (int a = 0; a < Q; ++a) l[a] = lam[a * N + n.i];
   const uint16_t fl = I.flags[n.i];
@@ -193,14 +171,17 @@ __global__ void k_adj_node(const InstDesc* __restrict__ insts, const double* __r
   const double a13 = ls[1] + ls[3], a24 = ls[2] + ls[4], a57 = ls[5] + ls[7], a68 = ls[6] + ls[8];
   const double d13 = ls[1] - ls[3], d24 = ls[2] - ls[4], d57 = ls[5] - ls[7], d68 = ls[6] - ls[8];
   const double s14 = a13 + a24, s58 = a57 + a68;
-  const double ae = (-4.0 * ls[0] - s14 + 2.0 * s58) / 36.0;
-  const double az = (4.0 * ls[0] - 2.0 * s14 + s58) / 36.0;
-  const double ajx = (d13 + d57 - d68) / 6.0;
-  const double aqx = (-2.0 * d13 + d57 - d68) / 12.0;
-  const double ajy = (d24 + d57 + d68) / 6.0;
-  const double aqy = (-2.0 * d24 + d57 + d68) / 12.0;
-  const double axx = (a13 - a24) / 4.0;
-  const double axy = (a57 - a68) / 4.0;
+  // the diagonal of M^-1 as products (a division by 36, 6 or 12 costs an
+  // FP64 division sequence; the gradient is checked to 1e-5, not bitwise)
+  constexpr double i36 = 1.0 / 36.0, i6 = 1.0 / 6.0, i12 = 1.0 / 12.0;
+  const double ae = (-4.0 * ls[0] - s14 + 2.0 * s58) * i36;
+  const double az = (4.0 * ls[0] - 2.0 * s14 + s58) * i36;
+  const double ajx = (d13 + d57 - d68) * i6;
+  const double aqx = (-2.0 * d13 + d57 - d68) * i12;
+  const double ajy = (d24 + d57 + d68) * i6;
+  const double aqy = (-2.0 * d24 + d57 + d68) * i12;
+  const double axx = (a13 - a24) * 0.25;
+  const double axy = (a57 - a68) * 0.25;
   // forward moments and velocity
   const double jx = fx[1] - fx[3] + fx[5] - fx[6] - fx[7] + fx[8];
   const double jy = fx[2] - fx[4] + fx[5] + fx[6] - fx[7] - fx[8];
@@ -304,7 +285,8 @@ __device__ __forceinline__ double stencil_adjoint(const InstDesc& I, const Node&
   return s;
 }
 
-__global__ void k_adj_gather(const InstDesc* __restrict__ insts, const double* __restrict__ dpsi,
+__global__ void k_adj_gather(const InstDesc* __restrict__ insts, const double* __restrict__ rho,
+                             const double* __restrict__ psi,
                              const double* __restrict__ lam_dir, const double2* __restrict__ lam_g,
                              const double* __restrict__ lam_psi_loc,
                              const double* __restrict__ lam_rho_loc,
@@ -342,22 +324,26 @@ __global__ void k_adj_gather(const InstDesc* __restrict__ insts, const double* _
         lpsi += stencil_adjoint(I, s, lam_g);
     }
   }
-  const double lrho = lam_rho_loc[n.i] + lpsi * dpsi[n.i];
+  // d psi / d rho = (d psi^2 / d rho) / (2 psi) on the branch of Eq. (15)
+  double slope;
+  psi2_and_slope(I, rho[n.i], slope);
+  const double lrho = lam_rho_loc[n.i] + lpsi * slope / (2.0 * psi[n.i]);
   for (int a = 0; a < Q; ++a) lam_out[a * N + n.i] = lam_dir[a * N + n.i] + lrho;
 }
 
 cudaError_t launch_adjoint_step(const InstDesc& h, const InstDesc* d_inst, const double* f,
-                                const double* lam_next, double* lam_out, double* grad,
-                                AdjScratch& s, cudaStream_t st) {
+                                const double* rho, double* psi, const double* lam_next,
+                                double* lam_out, double* grad, AdjScratch& s, cudaStream_t st) {
   const long long N = h.plane;
-  const int tb = 256;
+  // 64-thread blocks: a 256 x 128 lattice gives 512 blocks, enough for
+  // every SM (256-thread blocks left 24 of 152 SMs idle and the rest with
+  // one block each, latency bound on the FP64 pipe)
+  const int tb = 64;
   const unsigned grid = (unsigned)((N + tb - 1) / tb);
-  k_adj_fields<<<grid, tb, 0, st>>>(d_inst, f, s.rho, s.psi, s.dpsi);
-  k_adj_ghost<<<grid, tb, 0, st>>>(d_inst, s.psi);
-  k_adj_walls<<<grid, tb, 0, st>>>(d_inst, lam_next, s.lamp, s.lamF_bc);
-  k_adj_node<<<grid, tb, 0, st>>>(d_inst, f, s.rho, s.psi, lam_next, s.lamp, s.lamF_bc, s.lam_dir,
+  k_adj_walls<<<grid, tb, 0, st>>>(d_inst, lam_next, s.lamp, s.lamF_bc, psi);
+  k_adj_node<<<grid, tb, 0, st>>>(d_inst, f, rho, psi, lam_next, s.lamp, s.lamF_bc, s.lam_dir,
                                   s.lam_g, s.lam_psi_loc, s.lam_rho_loc, s.lam_A);
-  k_adj_gather<<<grid, tb, 0, st>>>(d_inst, s.dpsi, s.lam_dir, s.lam_g, s.lam_psi_loc,
+  k_adj_gather<<<grid, tb, 0, st>>>(d_inst, rho, psi, s.lam_dir, s.lam_g, s.lam_psi_loc,
                                     s.lam_rho_loc, s.lam_A, lam_out, grad);
   return cudaGetLastError();
 }

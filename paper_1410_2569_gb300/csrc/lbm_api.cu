@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -94,6 +95,9 @@ struct lbm_ctx {
   // per-item count of finished steps
   int *d_nbr_off = nullptr, *d_nbr = nullptr;
   unsigned* d_done = nullptr;
+  // host copies of the items and of those lists (lbm_get_work_items)
+  std::vector<WorkItem> h_items;
+  std::vector<int> h_nbr_off, h_nbr;
   int parity = 0;
   long t = 0;
   int bx = 0, h = 0, persistent = 0, use_graph = 0, stages = 0;
@@ -603,6 +607,9 @@ static lbm_status build_items(lbm_ctx* c) {
   CK(cudaMalloc(&c->d_items, items.size() * sizeof(WorkItem)));
   CK(cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
   c->n_items = (int)items.size();
+  c->h_items = items;
+  c->h_nbr_off.assign(items.size() + 1, 0);
+  c->h_nbr.clear();
   cudaFree(c->d_nbr_off);
   cudaFree(c->d_nbr);
   cudaFree(c->d_done);
@@ -616,6 +623,8 @@ static lbm_status build_items(lbm_ctx* c) {
     }
     std::vector<int> off, nb;
     strip_neighbours(items, shape, cols, off, nb);
+    c->h_nbr_off = off;
+    c->h_nbr = nb;
     CK(cudaMalloc(&c->d_nbr_off, off.size() * sizeof(int)));
     CK(cudaMemcpy(c->d_nbr_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&c->d_nbr, std::max<size_t>(nb.size(), 1) * sizeof(int)));
@@ -1223,6 +1232,20 @@ extern "C" lbm_status lbm_selftest_fp32_math(long n, const float* x, float* out)
   return LBM_OK;
 }
 
+extern "C" lbm_status lbm_selftest_fp64_math(long n, const double* x, double* out) {
+  if (!x || !out || n < 1) return fail(LBM_ERR_ARG, "need x, out and n >= 1");
+  double *dx = nullptr, *dout = nullptr;
+  cudaError_t e = cudaMalloc(&dx, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dout, 2 * n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(dx, x, n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_math_selftest64(dx, dout, n, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, 2 * n * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(dx);
+  cudaFree(dout);
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "math selftest: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
 extern "C" lbm_status lbm_selftest_fp64_rate(double* ops_per_s) {
   if (!ops_per_s) return fail(LBM_ERR_ARG, "ops_per_s is NULL");
   cudaError_t e = measure_fp64_rate(ops_per_s);
@@ -1353,23 +1376,22 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, long T, double theta_target, doubl
   // checkpoints every k steps: the library state (f*, F at walls) and parity
   const long k = (long)ceil(sqrt((double)T));
   const long nck = (T + k - 1) / k;
-  DevBuf ck, seg, lamA, lamB, grad, scr;
+  DevBuf ck, seg, segrp, lamA, lamB, grad, scr;
   const size_t ck_one = (fN + 2 * N) * sizeof(double);
   CK(cudaMalloc(&ck.p, nck * ck_one));
+  // one segment of recomputed forward states: f(t), and rho(t), psi(t)
   CK(cudaMalloc(&seg.p, (size_t)k * fN * sizeof(double)));
+  CK(cudaMalloc(&segrp.p, (size_t)k * 2 * N * sizeof(double)));
   CK(cudaMalloc(&lamA.p, fN * sizeof(double)));
   CK(cudaMalloc(&lamB.p, fN * sizeof(double)));
   CK(cudaMalloc(&grad.p, N * sizeof(double)));
   CK(cudaMemsetAsync(grad.p, 0, N * sizeof(double), c->stream));
   // scratch of the reverse step
-  const size_t scr_doubles = 3 * N + fN + 2 * N + fN + 2 * N + 2 * N + 2 * N;
+  const size_t scr_doubles = fN + 2 * N + fN + 2 * N + 2 * N + 2 * N;
   CK(cudaMalloc(&scr.p, scr_doubles * sizeof(double)));
   AdjScratch S;
   {
     double* q = (double*)scr.p;
-    S.rho = q; q += N;
-    S.psi = q; q += N;
-    S.dpsi = q; q += N;
     S.lamp = q; q += fN;
     S.lamF_bc = (double2*)q; q += 2 * N;
     S.lam_dir = q; q += fN;
@@ -1395,11 +1417,19 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, long T, double theta_target, doubl
     return LBM_OK;
   };
   const long t0 = c->t;
-  // forward pass with checkpoints
+  // forward pass with checkpoints (each segment's steps replayed from a
+  // CUDA graph of the context)
+  const int saved_graph = c->use_graph;
+  c->use_graph = 1;
   for (long ci = 0; ci < nck; ++ci) {
-    if ((st = save(ci)) != LBM_OK) return st;
-    if ((st = lbm_step(c, std::min(k, T - ci * k))) != LBM_OK) return st;
+    if ((st = save(ci)) == LBM_OK) st = lbm_step(c, std::min(k, T - ci * k));
+    if (st != LBM_OK) {
+      c->use_graph = saved_graph;
+      c->persistent = saved_persistent;
+      return st;
+    }
   }
+  c->use_graph = saved_graph;
   st = lbm_sync(c);
   if (st != LBM_OK) return st;
   const int final_parity = c->parity;
@@ -1430,23 +1460,71 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, long T, double theta_target, doubl
                      c->stream));
   double* lam_next = (double*)lamA.p;
   double* lam_cur = (double*)lamB.p;
+  // One segment: recompute f(t) of its len steps from the restored
+  // checkpoint, then len reverse steps.  The launches of a segment are
+  // captured once per (len, starting parity, which buffer holds lam) and
+  // replayed from a CUDA graph: the kernels of a 256 x 128 lattice last a
+  // few microseconds each, so launch gaps would otherwise dominate.
+  auto enqueue_segment = [&](long len, int p0, double* ln, double* lc,
+                             cudaStream_t s) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    int par = p0;
+    for (long q = 0; q < len && e == cudaSuccess; ++q) {
+      double* fs = (double*)seg.p + q * fN;
+      double* rs = (double*)segrp.p + q * 2 * N;
+      e = launch_macro(c->prec, I.desc, c->d_desc, par, rs, rs + N, nullptr, nullptr, fs, s,
+                       false);
+      if (e == cudaSuccess) e = launch_one_step(c, par, s);
+      par ^= 1;
+    }
+    for (long q = len - 1; q >= 0 && e == cudaSuccess; --q) {
+      const double* fs = (const double*)seg.p + q * fN;
+      double* rs = (double*)segrp.p + q * 2 * N;
+      e = launch_adjoint_step(I.desc, c->d_desc, fs, rs, rs + N, ln, lc, (double*)grad.p, S, s);
+      std::swap(ln, lc);
+    }
+    return e;
+  };
+  std::map<std::tuple<long, int, int>, cudaGraphExec_t> seg_graphs;
+  cudaStream_t cap = nullptr;
+  auto release = [&]() {
+    cudaStreamSynchronize(c->stream);  // no replay still pending
+    for (auto& kv : seg_graphs) cudaGraphExecDestroy(kv.second);
+    if (cap) cudaStreamDestroy(cap);
+  };
   for (long ci = nck - 1; ci >= 0; --ci) {
     const long len = std::min(k, T - ci * k);
-    if ((st = restore(ci)) != LBM_OK) return st;
-    // recompute f(t) for the segment
-    for (long s = 0; s < len; ++s) {
-      double* fs = (double*)seg.p + s * fN;
-      CK(launch_macro(c->prec, I.desc, c->d_desc, c->parity, c->d_rho, c->d_psi, nullptr,
-                      nullptr, fs, c->stream));
-      if ((st = lbm_step(c, 1)) != LBM_OK) return st;
+    if ((st = restore(ci)) != LBM_OK) {
+      release();
+      return st;
     }
-    for (long s = len - 1; s >= 0; --s) {
-      const double* fs = (const double*)seg.p + s * fN;
-      CK(launch_adjoint_step(I.desc, c->d_desc, fs, lam_next, lam_cur, (double*)grad.p, S,
-                             c->stream));
-      std::swap(lam_next, lam_cur);
+    const auto key = std::make_tuple(len, c->parity, lam_next == (double*)lamA.p ? 0 : 1);
+    auto it = seg_graphs.find(key);
+    cudaError_t e = cudaSuccess;
+    if (it == seg_graphs.end()) {
+      if (!cap) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+      cudaGraph_t g = nullptr;
+      if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        e = enqueue_segment(len, c->parity, lam_next, lam_cur, cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess) e = e2;
+      }
+      cudaGraphExec_t ge = nullptr;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e == cudaSuccess) it = seg_graphs.emplace(key, ge).first;
     }
+    if (e == cudaSuccess) e = cudaGraphLaunch(it->second, c->stream);
+    if (e != cudaSuccess) {
+      release();
+      c->persistent = saved_persistent;
+      return fail(LBM_ERR_CUDA, "adjoint segment: %s", cudaGetErrorString(e));
+    }
+    c->parity ^= (int)(len & 1);
+    if (len & 1) std::swap(lam_next, lam_cur);
   }
+  release();
   // back to the state after the forward pass
   c->parity = final_parity;
   CK(cudaMemcpyAsync(I.f[final_parity], fin.p, fbytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -1673,6 +1751,28 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, int steps, int* bx_out, int* h_ou
 
 // The strips of one nx x ny lattice in h-row segments (h > 0) and their
 // dependency lists as the persistent warp strips use them, on the host only.
+extern "C" lbm_status lbm_get_work_items(const lbm_ctx* c, int* n_items, int* items4, int* off,
+                                         int* nbr, int cap, int* n_nbr) {
+  if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
+  if (!n_items || !n_nbr) return fail(LBM_ERR_ARG, "n_items and n_nbr must not be NULL");
+  *n_items = (int)c->h_items.size();
+  *n_nbr = (int)c->h_nbr.size();
+  if (!items4 || !off || !nbr) return LBM_OK;  // sizes only
+  if ((long long)c->h_items.size() * 4 > cap || (long long)c->h_nbr.size() > cap ||
+      (long long)c->h_nbr_off.size() > cap)
+    return fail(LBM_ERR_ARG, "cap too small: %d items, %d neighbours", *n_items, *n_nbr);
+  for (size_t i = 0; i < c->h_items.size(); ++i) {
+    const WorkItem& w = c->h_items[i];
+    items4[4 * i] = w.inst;
+    items4[4 * i + 1] = w.x0;
+    items4[4 * i + 2] = w.y0;
+    items4[4 * i + 3] = w.y1;
+  }
+  for (size_t i = 0; i < c->h_nbr_off.size(); ++i) off[i] = c->h_nbr_off[i];
+  for (size_t i = 0; i < c->h_nbr.size(); ++i) nbr[i] = c->h_nbr[i];
+  return LBM_OK;
+}
+
 extern "C" lbm_status lbm_strip_neighbours(int nx, int ny, int h, int* n_items, int* items3,
                                            int* off, int* nbr, int cap, int* n_nbr) {
   if (nx < 3 || ny < 3 || h < 1) return fail(LBM_ERR_ARG, "need nx, ny >= 3 and h >= 1");

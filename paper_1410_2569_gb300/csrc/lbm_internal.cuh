@@ -124,16 +124,18 @@ size_t tma_smem_bytes(int bx, int S);
 
 // scratch of one reverse step (lbm_adjoint.cu), FP64, N nodes
 struct AdjScratch {
-  double *rho = nullptr, *psi = nullptr, *dpsi = nullptr;
   double* lamp = nullptr;  // [9][N]
   double2* lamF_bc = nullptr;
   double* lam_dir = nullptr;  // [9][N]
   double2 *lam_g = nullptr, *lam_A = nullptr;
   double *lam_psi_loc = nullptr, *lam_rho_loc = nullptr;
 };
+// one reverse step from the forward state f(t) with its rho and psi on
+// fluid nodes, as launch_macro gives them with ghost = false (the step fills
+// the ghost psi of the solid nodes in place)
 cudaError_t launch_adjoint_step(const InstDesc& h, const InstDesc* d_inst, const double* f,
-                                const double* lam_next, double* lam_out, double* grad,
-                                AdjScratch& s, cudaStream_t st);
+                                const double* rho, double* psi, const double* lam_next,
+                                double* lam_out, double* grad, AdjScratch& s, cudaStream_t st);
 
 // FP64 pipe throughput of the current device, DFMA instructions per second
 // (lbm_kernels.cu)
@@ -141,6 +143,8 @@ cudaError_t measure_fp64_rate(double* ops_per_s);
 
 // FP32 reciprocal / square root self-test (lbm_kernels.cu)
 cudaError_t launch_math_selftest(const float* d_x, float* d_out, long n, cudaStream_t s);
+// FP64 reciprocal self-test (lbm_kernels.cu)
+cudaError_t launch_math_selftest64(const double* d_x, double* d_out, long n, cudaStream_t s);
 
 // records the calling thread's lbm_last_error() message and returns s
 lbm_status set_error(lbm_status s, const char* fmt, ...);
@@ -177,7 +181,9 @@ cudaError_t launch_init_all(int prec, const InstDesc* d_inst, const long long* d
 cudaError_t launch_macro_all(int prec, const InstDesc* d_inst, const long long* d_offs, int n,
                              long long total, int parity, double* d_rho, double* d_psi,
                              double* d_ux, double* d_uy, cudaStream_t s);
+// ghost = false leaves psi on solid nodes unset (the adjoint fills it in its
+// reverse step)
 cudaError_t launch_macro(int prec, const InstDesc& h_inst, const InstDesc* d_inst, int parity,
                          double* d_rho, double* d_psi, double* d_ux, double* d_uy, double* d_f,
-                         cudaStream_t s);
+                         cudaStream_t s, bool ghost = true);
 }  // namespace lbm

@@ -49,3 +49,21 @@ def test_special_arguments(cuda):
     o = _run(x)
     assert o[0, 2] == 0.0 and np.isnan(o[2, 2]) and np.isnan(o[4, 2])
     assert np.isinf(o[3, 2])
+
+
+def test_fp64_reciprocal_within_one_ulp(cuda):
+    """The FP64 step's reciprocal (hardware approximation and two
+    Newton-Raphson steps) against CUDA's correctly rounded one, over the
+    densities and relaxation times of the step and over the binades of the
+    normal numbers the step can meet."""
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.uniform(1e-3, 600.0, 200000), rng.uniform(0.5, 20.0, 50000),
+                        2.0 ** rng.uniform(-300, 300, 200000),
+                        2.0 ** np.arange(-300, 301, dtype=np.float64)])
+    out = np.zeros(2 * x.size)
+    L = lbm.load()
+    assert L.lbm_selftest_fp64_math(x.size, x.ctypes.data, out.ctypes.data) == 0
+    o = out.reshape(-1, 2)
+    ulps = np.abs(o[:, 0].view(np.int64) - o[:, 1].view(np.int64))
+    assert ulps.max() <= 1, ulps.max()
+    assert np.mean(ulps == 0) > 0.9

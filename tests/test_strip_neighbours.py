@@ -62,3 +62,55 @@ def test_strip_neighbours_arguments():
     buf = np.zeros(4, np.int32)
     assert L.lbm_strip_neighbours(64, 40, 4, ctypes.byref(n), buf.ctypes.data, buf.ctypes.data,
                                   buf.ctypes.data, 4, ctypes.byref(m)) == ERR_ARG
+
+
+def _ctx_lists(lat):
+    L = lbm.load()
+    n_items, n_nbr = ctypes.c_int(), ctypes.c_int()
+    assert L.lbm_get_work_items(lat._h, ctypes.byref(n_items), None, None, None, 0,
+                                ctypes.byref(n_nbr)) == 0
+    n = n_items.value
+    cap = max(4 * n, n_nbr.value, n + 1)
+    items, off, nbr = (np.zeros(cap, np.int32) for _ in range(3))
+    assert L.lbm_get_work_items(lat._h, ctypes.byref(n_items), items.ctypes.data,
+                                off.ctypes.data, nbr.ctypes.data, cap, ctypes.byref(n_nbr)) == 0
+    return items[:4 * n].reshape(n, 4), [nbr[off[i]:off[i + 1]].tolist() for i in range(n)]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("shape", [dict(), dict(h=3), dict(h=2, bx=64)])
+def test_context_lists_of_a_persistent_batch_match_brute_force(cuda, prec, shape):
+    """The items and dependency lists a persistent warp-strip batch actually
+    runs with (lbm_get_work_items): several instances of uneven sizes (odd
+    heights among them), the automatic segment heights and fixed ones.  Item
+    j is listed for item i exactly when both belong to one instance and a
+    node of j lies within 4 nodes of one of i along x and along y
+    (periodic); items of other instances are never listed."""
+    from paper_1410_2569_gb300 import inputs
+    shapes = [(64, 40), (130, 48), (96, 70), (33, 21), (257, 37)]
+    specs = [dict(nx=nx, ny=ny, params=lbm.default_params(prec=prec),
+                  solid=inputs.flat_walls(nx, ny), fsi="modified", gw=0.1) for nx, ny in shapes]
+    lat = lbm.Lattice(specs)
+    lat.set_launch(persistent=True, **shape)
+    items, lists = _ctx_lists(lat)
+    for k, (nx, ny) in enumerate(shapes):
+        cover = np.zeros((ny, nx), int)
+        for inst, x0, y0, y1 in items:
+            if inst == k:
+                cover[y0:y1, x0:min(nx, x0 + 30)] += 1
+        assert (cover == 1).all(), k
+    heights = {int(y1 - y0) for _, _, y0, y1 in items}
+    assert len(heights) > 1  # segments of different heights (odd ny, short last segments)
+    for i, (k, x0, y0, y1) in enumerate(items):
+        nx, ny = shapes[k]
+        listed = set(lists[i])
+        assert len(listed) == len(lists[i]) and i in listed
+        for j, (kj, u0, v0, v1) in enumerate(items):
+            near = (kj == k and _gap(x0, min(nx, x0 + 30), u0, min(nx, u0 + 30), nx) <= 4 and
+                    _gap(y0, y1, v0, v1, ny) <= 4)
+            assert (j in listed) == near, (i, j)
+    # one launch per step: the same items, no lists
+    lat.set_launch()
+    items2, lists2 = _ctx_lists(lat)
+    assert all(not ls for ls in lists2) and len(items2) > 0

@@ -51,6 +51,39 @@ def test_noalloc_matches_diagnostics_on_two_calls_in_a_row(cuda):
         assert abs(got["theta_deg"] - ref["theta_deg"]) <= 1e-8, call
 
 
+def test_noalloc_without_a_solid_mask(cuda):
+    """solid = NULL: a lattice with no solid nodes (a free droplet, periodic
+    both ways), compared with lbm_diagnostics on the same state, two calls
+    in a row."""
+    import torch
+
+    import paper_1410_2569_gb300 as lbm
+    from paper_1410_2569_gb300._lib import LbmDiag
+
+    nx, ny, x_ref, y_w = 96, 80, 48.0, 40.0
+    p = lbm.default_params()
+    lat = lbm.Lattice.single(nx, ny, p, None, "modified", 0.0)
+    lat.init_droplet(x_ref, y_w, 18.0, 2.0)
+    L = lbm.load()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    level = 0.5 * (p["rho_L"] + p["rho_V"])
+    for call in range(2):
+        lat.step(200)
+        ref = lat.diagnostics(y_w=y_w, x_ref=x_ref, d_min=3.0)
+        f = lat.fields(device=True)
+        torch.cuda.synchronize()
+        out = LbmDiag()
+        st = L.lbm_diagnostics_noalloc(nx, ny, _ptr(f["rho"]), _ptr(f["ux"]), _ptr(f["uy"]),
+                                       None, level, y_w, x_ref, 3.0, stream, ctypes.byref(out))
+        assert st == 0, L.lbm_last_error()
+        got = out.as_dict()
+        assert got["status"] == ref["status"], call
+        assert got["n_contour"] == ref["n_contour"] > 20, call
+        assert abs(got["mass"] - ref["mass"]) <= 1e-11 * ref["mass"], call
+        for k in ("rho_max", "rho_min", "u_max", "radius", "xc", "yc", "fit_rms", "theta_deg"):
+            assert abs(got[k] - ref[k]) <= 1e-9 * max(1.0, abs(ref[k])), (call, k, got[k], ref[k])
+
+
 def test_noalloc_rejects_sizes_beyond_its_limit(cuda):
     import torch
 
