@@ -67,11 +67,15 @@ class LbmError(RuntimeError):
 _lib = None
 
 
-def load(path=LIB_PATH):
-    """Load liblbm.so.  There is no fallback: a missing library is an error."""
+def load(path=None):
+    """Load liblbm.so (or the library named by the LBM_LIBRARY environment
+    variable, e.g. the checked build liblbm_check.so).  There is no
+    fallback: a missing library is an error."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = os.environ.get("LBM_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"liblbm.so not found at {path}; build it with "
                           "`python -c 'import __graft_entry__ as g; g.build()'`")

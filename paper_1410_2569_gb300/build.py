@@ -15,6 +15,11 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm.so")
+# the checked build: every index of the step kernels tested against its
+# buffer, a bad one latched as an error (LBM_ERR_STATE at the next
+# synchronising call) instead of an access
+LIB_CHECK = os.path.join(PKG, "liblbm_check.so")
+CHECK_FLAGS = ["-DLBM_BOUNDS_CHECK"]
 SOURCES = ["lbm_kernels.cu", "lbm_diag.cu", "lbm_adjoint.cu", "lbm_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -36,15 +41,23 @@ def _deps():
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force=False, verbose=False, extra=()):
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
+def build(force=False, verbose=False, extra=(), checked=True):
+    """Build liblbm.so and (checked=True) liblbm_check.so, all translation
+    units of both compiled in parallel; returns the path of liblbm.so."""
+    targets = [(LIB, list(extra), "")]
+    if checked:
+        targets.append((LIB_CHECK, list(extra) + CHECK_FLAGS, "_check"))
+    todo = [t for t in targets
+            if force or not os.path.exists(t[0]) or os.path.getmtime(t[0]) < _deps()]
+    if not todo:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nv = nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nv] + _flags(extra) + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(job):
+        src, flags, tag = job
+        obj = os.path.join(BUILD, src.replace(".cu", tag + ".o"))
+        cmd = [nv] + _flags(flags) + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -52,14 +65,17 @@ def build(force=False, verbose=False, extra=()):
             sys.stderr.write(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp"
-    cmd = [nv] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    jobs = [(src, flags, tag) for _, flags, tag in todo for src in SOURCES]
+    with cf.ThreadPoolExecutor(len(jobs)) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    for k, (lib, _, _) in enumerate(todo):
+        mine = objs[k * len(SOURCES):(k + 1) * len(SOURCES)]
+        tmp = lib + ".tmp"
+        cmd = [nv] + ARCH + ["-shared", "-o", tmp] + mine + ["-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

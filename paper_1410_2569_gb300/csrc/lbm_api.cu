@@ -940,6 +940,8 @@ extern "C" lbm_status lbm_sync(lbm_ctx* c) {
   CK(cudaMemcpy(&h[0], c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&h[1], c->d_barrier + 1, sizeof(int), cudaMemcpyDeviceToHost));
   const int bits = h[0] | h[1];
+  if (bits & ERR_BOUNDS)
+    return fail(LBM_ERR_STATE, "an index of a step kernel fell outside its buffer (checked build)");
   if (bits & ERR_TIMEOUT)
     return fail(LBM_ERR_TIMEOUT, "a grid barrier of the persistent step kernel timed out");
   if (bits & ERR_NONFINITE)

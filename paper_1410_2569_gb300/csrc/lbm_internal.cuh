@@ -105,7 +105,22 @@ struct WorkItem {
   int inst, x0, y0, y1;
 };
 
-enum : int { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
+enum : int { ERR_NONFINITE = 1, ERR_TIMEOUT = 2, ERR_BOUNDS = 4 };
+
+// Index checks of the checked build (compiled with -DLBM_BOUNDS_CHECK into
+// liblbm_check.so): every global and shared-memory index of the step
+// kernels is tested against its buffer before the access; a bad index
+// latches ERR_BOUNDS in *err and the access is skipped (a load gives 0), so
+// nothing traps.  In the normal build the test is the constant true.
+#ifdef LBM_BOUNDS_CHECK
+__device__ __forceinline__ bool in_bounds(long long i, long long n, int* err) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(err, ERR_BOUNDS);
+  return false;
+}
+#else
+__device__ __forceinline__ constexpr bool in_bounds(long long, long long, int*) { return true; }
+#endif
 
 // step pipelines (launch_step's `stages` argument): block rows with register
 // prefetch, warp strips (two rows per lane with FP32 storage, one otherwise),
