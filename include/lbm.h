@@ -105,6 +105,14 @@ typedef enum { LBM_OMEGA_W = 0, LBM_OMEGA_CS2W = 1 } lbm_omega;
    but density summed and psi evaluated in IEEE FP64 instructions. */
 typedef enum { LBM_FP64 = 0, LBM_FP32_SHIFTED = 1, LBM_FP32_SHIFTED_F64 = 2 } lbm_precision;
 
+/* tau_nu between the phases when tau_nu_L != tau_nu_V (Sec. III.C gives
+   the liquid and vapour viscosities only).  LBM_VISC_TAU_LINEAR: tau_nu
+   linear in rho (equivalently the kinematic viscosity nu = (tau_nu - 1/2)
+   cs^2 linear in rho) (default).  LBM_VISC_MU_LINEAR: the dynamic
+   viscosity mu = rho nu linear in rho, tau_nu = 1/2 + mu(rho) / (rho cs^2).
+   Both clamped to [min, max] of the two end values. */
+typedef enum { LBM_VISC_TAU_LINEAR = 0, LBM_VISC_MU_LINEAR = 1 } lbm_visc;
+
 typedef struct {
   lbm_eos eos;
   /* Eq. (15): theta_V, theta_M, theta_L in units of cs^2, then rho_1, rho_2;
@@ -116,7 +124,7 @@ typedef struct {
   /* relaxation times of Eq. (2) */
   double tau_rho, tau_e, tau_zeta, tau_j, tau_q;
   /* tau_nu in liquid and vapour (Sec. III.C); when they differ tau_nu varies
-     linearly in rho between rho_V and rho_L, clamped to the two values.
+     between rho_V and rho_L as `visc` says, clamped to the two values.
      rho_L and rho_V also set the contact-angle level (rho_L + rho_V) / 2. */
   double tau_nu_L, tau_nu_V, rho_L, rho_V;
   lbm_wall wall;
@@ -124,6 +132,7 @@ typedef struct {
   lbm_omega omega;
   lbm_precision prec;
   double rho_ref; /* shift of the FP32 storage (ignored for LBM_FP64) */
+  lbm_visc visc;  /* tau_nu between the phases (used when tau_nu_L != tau_nu_V) */
 } lbm_params;
 
 /* One lattice of a batch (lbm_create_batch). */
@@ -153,7 +162,7 @@ typedef struct {
    theta_M = -0.04 cs^2, theta_L = cs^2, rho_1 = 1.36, rho_2 = 481.04, G = -1,
    sigma = 0.084, tau_rho = tau_j = 1, 1/tau_e = 1/tau_zeta = 0.8,
    1/tau_q = 1.1, tau_nu = 1.1, rho_L = 500, rho_V = 1, NEQ wall, COPY ghost,
-   LBM_OMEGA_W, LBM_FP64, rho_ref = rho_V. */
+   LBM_OMEGA_W, LBM_FP64, rho_ref = rho_V, LBM_VISC_TAU_LINEAR. */
 lbm_status lbm_default_params(lbm_params* p);
 
 /* Creates a context holding one lattice.  solid: [ny][nx] host array (NULL =

@@ -18,6 +18,7 @@ WALL = {"neq": 0, "bb": 1}
 GHOST = {"copy": 0, "mirror": 1, "zero": 2, "skip": 3, "mean": 4}
 EOS = {"pl": 0, "cs": 1}
 OMEGA = {"w": 0, "cs2w": 1}
+VISC = {"tau": 0, "mu": 1}
 
 
 class OracleParams(ctypes.Structure):
@@ -31,7 +32,8 @@ class OracleParams(ctypes.Structure):
                 ("rho_L", ctypes.c_double), ("rho_V", ctypes.c_double),
                 ("wall", ctypes.c_int), ("ghost", ctypes.c_int), ("omega", ctypes.c_int),
                 ("eos", ctypes.c_int), ("cs_a", ctypes.c_double), ("cs_b", ctypes.c_double),
-                ("cs_R", ctypes.c_double), ("cs_T", ctypes.c_double)]
+                ("cs_R", ctypes.c_double), ("cs_T", ctypes.c_double),
+                ("visc", ctypes.c_int)]
 
 
 class OracleDiag(ctypes.Structure):
@@ -93,7 +95,7 @@ def paper_params(**over):
     d = dict(kV=0.64, kM=-0.04, kL=1.0, rho_1=1.36, rho_2=481.04, G=-1.0, sigma=0.084,
              tau_rho=1.0, tau_e=1.0 / 0.8, tau_zeta=1.0 / 0.8, tau_j=1.0, tau_q=1.0 / 1.1,
              tau_nu_L=1.1, tau_nu_V=1.1, rho_L=500.0, rho_V=1.0, wall="neq", ghost="copy",
-             omega="w", eos="pl", cs_a=1.0, cs_b=4.0, cs_R=1.0, cs_T=0.0)
+             omega="w", eos="pl", cs_a=1.0, cs_b=4.0, cs_R=1.0, cs_T=0.0, visc="tau")
     d.update(over)
     return d
 
@@ -107,6 +109,8 @@ def to_struct(params):
     p["eos"] = EOS[p["eos"]] if isinstance(p["eos"], str) else p["eos"]
     for k, v in (("cs_a", 1.0), ("cs_b", 4.0), ("cs_R", 1.0), ("cs_T", 0.0)):
         p.setdefault(k, v)
+    p.setdefault("visc", "tau")
+    p["visc"] = VISC[p["visc"]] if isinstance(p["visc"], str) else p["visc"]
     return OracleParams(**{k: p[k] for k, _ in OracleParams._fields_})
 
 

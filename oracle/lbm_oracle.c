@@ -38,7 +38,8 @@
  *     fluid nodes next to the solid node along the axes, COPY extended to
  *     walls of any shape (a ghost layer below rough surfaces, Sec. III.B).
  *   - tau_nu varies linearly with rho between rho_V and rho_L (clamped)
- *     when the liquid and vapour values differ (Sec. III.C).
+ *     when the liquid and vapour values differ (Sec. III.C); the option
+ *     ORC_VISC_MU makes the dynamic viscosity rho nu linear in rho instead.
  *   - M is the orthogonal D2Q9 basis whose rows give the equilibria of
  *     Eq. (3): 1, -4+3|e|^2, 4-21|e|^2/2+9|e|^4/2, e_x, (3|e|^2-5)e_x,
  *     e_y, (3|e|^2-5)e_y, e_x^2-e_y^2, e_x e_y.
@@ -346,7 +347,16 @@ static void macroscopic(oracle_lbm* o) {
 
 static double tau_nu_of(const oracle_params* p, double rho) {
   if (p->tau_nu_L == p->tau_nu_V) return p->tau_nu_L;
-  double t = p->tau_nu_V + (rho - p->rho_V) / (p->rho_L - p->rho_V) * (p->tau_nu_L - p->tau_nu_V);
+  const double frac = (rho - p->rho_V) / (p->rho_L - p->rho_V);
+  double t;
+  if (p->visc == ORC_VISC_MU) {
+    /* mu = rho nu linear in rho, nu = (tau - 1/2) cs^2 */
+    const double muV = p->rho_V * (p->tau_nu_V - 0.5) * cs2;
+    const double muL = p->rho_L * (p->tau_nu_L - 0.5) * cs2;
+    t = 0.5 + (muV + frac * (muL - muV)) / rho / cs2;
+  } else {
+    t = p->tau_nu_V + frac * (p->tau_nu_L - p->tau_nu_V);
+  }
   double lo = p->tau_nu_L < p->tau_nu_V ? p->tau_nu_L : p->tau_nu_V;
   double hi = p->tau_nu_L < p->tau_nu_V ? p->tau_nu_V : p->tau_nu_L;
   return t < lo ? lo : (t > hi ? hi : t);

@@ -40,6 +40,12 @@ enum { ORC_OMEGA_W = 0, ORC_OMEGA_CS2W = 1 };
    Starling, p = rho R T (1 + e + e^2 - e^3) / (1 - e)^3 - a rho^2 with
    e = b rho / 4 (an option: the paper uses Eq. (15) only). */
 enum { ORC_EOS_PL = 0, ORC_EOS_CS = 1 };
+/* tau_nu between the phases when tau_nu_L != tau_nu_V (Sec. III.C gives the
+   two end values only).  ORC_VISC_TAU: tau_nu linear in rho (equivalently
+   the kinematic viscosity nu = (tau_nu - 1/2) cs^2 linear in rho).
+   ORC_VISC_MU: the dynamic viscosity mu = rho nu linear in rho,
+   tau_nu = 1/2 + 3 mu(rho) / rho.  Both clamped to the two end values. */
+enum { ORC_VISC_TAU = 0, ORC_VISC_MU = 1 };
 
 typedef struct {
   /* Eq. (15): theta_V, theta_M, theta_L in units of cs^2, spinodal rho_1, rho_2 */
@@ -48,12 +54,13 @@ typedef struct {
   double sigma;      /* Eq. (9) mechanical-stability parameter */
   /* relaxation times of Eq. (2): tau_rho, tau_e, tau_zeta, tau_j, tau_q */
   double tau_rho, tau_e, tau_zeta, tau_j, tau_q;
-  /* tau_nu in the liquid and vapour phase; interpolated linearly in rho
-     between rho_V and rho_L (clamped) when they differ */
+  /* tau_nu in the liquid and vapour phase; interpolated between rho_V and
+     rho_L (clamped) when they differ, as `visc` says */
   double tau_nu_L, tau_nu_V, rho_L, rho_V;
   int wall, ghost, omega;
   int eos;                     /* ORC_EOS_* */
   double cs_a, cs_b, cs_R, cs_T; /* Carnahan-Starling constants */
+  int visc;                    /* ORC_VISC_* */
 } oracle_params;
 
 typedef struct {

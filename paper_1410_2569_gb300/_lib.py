@@ -11,6 +11,7 @@ GHOST = {"copy": 0, "mirror": 1, "zero": 2, "skip": 3, "mean": 4}
 OMEGA = {"w": 0, "cs2w": 1}
 EOS = {"pl": 0, "cs": 1}
 PREC = {"fp64": 0, "fp32": 1, "fp32_f64": 2}
+VISC = {"tau": 0, "mu": 1}
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
           4: "LBM_ERR_NONFINITE", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_STATE"}
 
@@ -36,7 +37,7 @@ class LbmParams(ctypes.Structure):
                 ("tau_nu_L", ctypes.c_double), ("tau_nu_V", ctypes.c_double),
                 ("rho_L", ctypes.c_double), ("rho_V", ctypes.c_double),
                 ("wall", ctypes.c_int), ("ghost", ctypes.c_int), ("omega", ctypes.c_int),
-                ("prec", ctypes.c_int), ("rho_ref", ctypes.c_double)]
+                ("prec", ctypes.c_int), ("rho_ref", ctypes.c_double), ("visc", ctypes.c_int)]
 
 
 class LbmInstanceDesc(ctypes.Structure):

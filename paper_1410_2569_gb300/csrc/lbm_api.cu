@@ -175,6 +175,8 @@ static lbm_status validate_params(const lbm_params* p) {
   if ((int)p->ghost < 0 || (int)p->ghost > 4) return fail(LBM_ERR_ARG, "unknown ghost %d", (int)p->ghost);
   if ((int)p->omega < 0 || (int)p->omega > 1) return fail(LBM_ERR_ARG, "unknown omega %d", (int)p->omega);
   if ((int)p->prec < 0 || (int)p->prec > 2) return fail(LBM_ERR_ARG, "unknown precision %d", (int)p->prec);
+  if ((int)p->visc < 0 || (int)p->visc > 1)
+    return fail(LBM_ERR_ARG, "unknown viscosity interpolation %d", (int)p->visc);
   if (!isfinite(p->rho_ref)) return fail(LBM_ERR_ARG, "rho_ref must be finite");
   return LBM_OK;
 }
@@ -305,6 +307,10 @@ static void fill_visc(Visc<T>& V, const lbm_params& p) {
   V.tau_lo = (T)std::min(p.tau_nu_L, p.tau_nu_V);
   V.tau_hi = (T)std::max(p.tau_nu_L, p.tau_nu_V);
   V.rho_V = (T)p.rho_V;
+  // dynamic viscosity mu = rho (tau - 1/2) cs^2 at the two ends, times 3
+  const double muV3 = p.rho_V * (p.tau_nu_V - 0.5), muL3 = p.rho_L * (p.tau_nu_L - 0.5);
+  V.muV3 = (T)muV3;
+  V.dmu3 = (T)((muL3 - muV3) / (p.rho_L - p.rho_V));
 }
 
 // The part of PhysDesc that the step kernels read: the viscosity (s_nu,
@@ -326,7 +332,7 @@ static void fill_desc(Inst& I, int prec, int* d_err) {
   d.fsi = (int)I.fsi;
   ph.wall = (int)p.wall;
   ph.ghost = (int)p.ghost;
-  d.var_nu = p.tau_nu_L != p.tau_nu_V;
+  d.var_nu = p.tau_nu_L == p.tau_nu_V ? 0 : (p.visc == LBM_VISC_MU_LINEAR ? 2 : 1);
   ph.omega_cs2w = p.omega == LBM_OMEGA_CS2W;
   ph.eos = (int)p.eos;
   if (p.eos == LBM_EOS_CARNAHAN_STARLING) {
@@ -1574,7 +1580,8 @@ static uint64_t ctx_hash(const lbm_ctx* c) {
     const double dv[] = {p.eos_p[0], p.eos_p[1], p.eos_p[2], p.eos_p[3], p.eos_p[4], p.G,
                          p.sigma, p.tau_rho, p.tau_e, p.tau_zeta, p.tau_j, p.tau_q, p.tau_nu_L,
                          p.tau_nu_V, p.rho_L, p.rho_V, p.rho_ref};
-    const int iv[] = {(int)p.eos, (int)p.wall, (int)p.ghost, (int)p.omega, (int)p.prec};
+    const int iv[] = {(int)p.eos, (int)p.wall, (int)p.ghost, (int)p.omega, (int)p.prec,
+                      (int)p.visc};
     h = fnv(h, dv, sizeof dv);
     h = fnv(h, iv, sizeof iv);
     h = fnv(h, I.solid.data(), I.solid.size());

@@ -54,10 +54,13 @@ struct Consts {
 // (the diagonal of M^-1 folded in), s_nu = 1 / tau_nu_L; or, with a
 // viscosity ratio, tau_nu(rho) = tauV + (rho - rho_V) dtau clamped to
 // [tau_lo, tau_hi] and the rates formed per node.
+// With the dynamic viscosity linear in rho (LBM_VISC_MU_LINEAR), tau_nu(rho)
+// = 1/2 + (muV + (rho - rho_V) dmu) / (rho cs^2), clamped likewise.
 template <typename T>
 struct Visc {
   T knu, hnu2, hnu4;
   T tauV, dtau, tau_lo, tau_hi, rho_V;
+  T muV3, dmu3;  // 3 mu_V and 3 dmu (mu / cs^2 with cs^2 = 1/3)
 };
 
 // The part of an instance descriptor fixed by its lbm_params.  The step
@@ -84,7 +87,7 @@ struct __align__(16) PhysDesc {
 struct __align__(16) InstDesc {
   int nx, ny;
   int fsi;
-  int var_nu;  // tau_nu_L != tau_nu_V: viscosity rates per node
+  int var_nu;  // 0: one viscosity; 1: tau_nu linear in rho; 2: mu linear in rho
   long long plane;  // nx * ny
   void* f[2];
   const uint16_t* flags;

@@ -7,7 +7,8 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import EOS, FSI, GHOST, OMEGA, PREC, WALL, LbmDiag, LbmInstanceDesc, LbmParams, check
+from ._lib import (EOS, FSI, GHOST, OMEGA, PREC, VISC, WALL, LbmDiag, LbmInstanceDesc, LbmParams,
+                   check)
 
 _PARAM_KEYS = ("G", "sigma", "tau_rho", "tau_e", "tau_zeta", "tau_j", "tau_q", "tau_nu_L",
                "tau_nu_V", "rho_L", "rho_V", "rho_ref")
@@ -20,7 +21,7 @@ def default_params(**over):
     check(_lib.load().lbm_default_params(ctypes.byref(p)))
     d = {k: getattr(p, k) for k in _PARAM_KEYS}
     d.update(kV=p.eos_p[0], kM=p.eos_p[1], kL=p.eos_p[2], rho_1=p.eos_p[3], rho_2=p.eos_p[4],
-             wall="neq", ghost="copy", omega="w", prec="fp64")
+             wall="neq", ghost="copy", omega="w", prec="fp64", visc="tau")
     d.update(over)
     return d
 
@@ -42,6 +43,7 @@ def to_struct(d):
         # Carnahan-Starling: a, b, R, T
         for j, (k, v) in enumerate((("cs_a", 1.0), ("cs_b", 4.0), ("cs_R", 1.0), ("cs_T", None))):
             p.eos_p[j] = float(d[k] if k in d or v is None else v)
+    p.visc = enum(d.get("visc", "tau"), VISC)
     p.wall = enum(d.get("wall", "neq"), WALL)
     p.ghost = enum(d.get("ghost", "copy"), GHOST)
     p.omega = enum(d.get("omega", "w"), OMEGA)

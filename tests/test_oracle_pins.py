@@ -471,7 +471,8 @@ def _brute_force_step(f, p, solid, gw, fsi):
     ZERO: 0), F_m (Eq. 7) and F_ads (Eqs. 10, 11,
     14 with omega = w), v (Eq. 6), m = M f with M built from its basis
     vectors, m* of Eq. (4) with the rates of Eq. (2) (tau_nu linear in rho
-    between rho_V and rho_L, clamped) and S of Eq. (9), f* = M^-1 m*, then
+    between rho_V and rho_L, or the dynamic viscosity rho nu linear in rho;
+    clamped) and S of Eq. (9), f* = M^-1 m*, then
     the pull of Eq. (5) with, at links from solid nodes, halfway bounce-back
     (p["wall"] == "bb") or the on-node rule of Sec. III.A (f2, f5, f6 at a
     wall below, mirrored above, with this step's force F)."""
@@ -512,8 +513,14 @@ def _brute_force_step(f, p, solid, gw, fsi):
     meq = rho * np.array([np.ones_like(rho), -2 + 3 * v2, 1 - 3 * v2, vx, -vx, vy, -vy,
                           vx ** 2 - vy ** 2, vx * vy])
     lo, hi = sorted((p["tau_nu_L"], p["tau_nu_V"]))
-    tnu = np.clip(p["tau_nu_V"] + (rho - p["rho_V"]) / (p["rho_L"] - p["rho_V"]) *
-                  (p["tau_nu_L"] - p["tau_nu_V"]), lo, hi)
+    frac = (rho - p["rho_V"]) / (p["rho_L"] - p["rho_V"])
+    if p.get("visc", "tau") == "mu":
+        # dynamic viscosity rho nu linear in rho, nu = (tau - 1/2) / 3
+        muV = p["rho_V"] * (p["tau_nu_V"] - 0.5) / 3
+        muL = p["rho_L"] * (p["tau_nu_L"] - 0.5) / 3
+        tnu = np.clip(0.5 + 3 * (muV + frac * (muL - muV)) / rho, lo, hi)
+    else:
+        tnu = np.clip(p["tau_nu_V"] + frac * (p["tau_nu_L"] - p["tau_nu_V"]), lo, hi)
     one = np.ones_like(rho)
     lam = np.array([one / p["tau_rho"], one / p["tau_e"], one / p["tau_zeta"], one / p["tau_j"],
                     one / p["tau_q"], one / p["tau_j"], one / p["tau_q"], 1 / tnu, 1 / tnu])
@@ -559,6 +566,8 @@ def _drop(nx, ny, x0, y0, R):
     dict(n=(8, 8), rho=lambda: 1 + 0.2 * _wave(8, 8)),
     dict(n=(8, 8), rho=lambda: 480 + 3 * _wave(8, 8)),
     dict(n=(8, 8), rho=lambda: _drop(8, 8, 3.5, 3.5, 2.5), over=dict(tau_nu_L=0.6, tau_nu_V=1.5)),
+    dict(n=(8, 8), rho=lambda: _drop(8, 8, 3.5, 3.5, 2.5),
+         over=dict(tau_nu_L=0.6, tau_nu_V=1.5, visc="mu")),
     # 12 x 10 between walls (solid rows 0 and 9, G_w on the bottom one):
     # the on-node wall rule for each interaction, halfway bounce-back
     dict(n=(12, 10), walls=True, fsi="modified", gw=0.1, rho=lambda: _drop(12, 10, 6, 0.5, 4)),
