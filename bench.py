@@ -14,6 +14,7 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -45,7 +46,8 @@ def profile_figures():
     kernel source than the one built now."""
     try:
         with open(PROFILE) as fh:
-            kv = dict(ln.strip("`* \n").split(": ", 1) for ln in fh if ": " in ln)
+            kv = dict(ln.strip().split(": ", 1) for ln in fh
+                      if re.match(r"[a-z0-9_-]+: ", ln))
     except OSError:
         return {}
     if kv.get("kernel-source-sha256", "").strip() != kernel_sha():
