@@ -205,12 +205,22 @@ lbm_status lbm_set_density(lbm_ctx* ctx, int inst, const double* rho, int src_is
    synchronising call. */
 lbm_status lbm_set_density_async(lbm_ctx* ctx, int inst, const double* rho, int src_is_device);
 
-/* Advances every instance by n time steps.  Asynchronous: returns after
-   enqueueing on the context's stream. */
+/* Advances every instance by n time steps of the method of Sec. II: per
+   node, streaming (Eq. 5, pull form) with the wall treatment of Sec. III.A
+   folded into the pull, density and velocity (Eq. 6), psi from the EOS
+   (Eq. 15, or the Carnahan-Starling option), the fluid-fluid force (Eq. 7),
+   the fluid-solid force (Eq. 10, 11 or 14), and the MRT collision (Eqs. 2-4)
+   with the forcing of Eq. 9.  Asynchronous: returns after enqueueing on the
+   context's stream; n = 0 is a no-op, n < 0 is LBM_ERR_ARG.  Device-side
+   errors (non-finite density, a timed-out persistent wait) latch in the
+   context and are returned by the next synchronising call. */
 lbm_status lbm_step(lbm_ctx* ctx, long n);
 
 /* Waits for the context's stream and for the host copies of the batch
-   calls below; returns a latched device error if any. */
+   calls below (an implementation call; the paper has no counterpart);
+   returns a latched device error if any (LBM_ERR_NONFINITE,
+   LBM_ERR_TIMEOUT, or LBM_ERR_STATE for an index that the checked build
+   caught); the error stays latched, so every later lbm_sync returns it. */
 lbm_status lbm_sync(lbm_ctx* ctx);
 
 long lbm_time(const lbm_ctx* ctx);
@@ -295,7 +305,9 @@ lbm_status lbm_set_gw_field(lbm_ctx* ctx, int inst, const double* gw);
 lbm_status lbm_adjoint(lbm_ctx* ctx, long T, double theta_target, double y_w, double x_ref,
                        double d_min, double* loss_out, double* theta_out, double* grad_gw);
 
-/* Launch shape of lbm_step: bx threads per block along x (a block covers
+/* Launch shape of lbm_step (an implementation call; the paper has no
+   counterpart, and the step it runs is the one of lbm_step whatever the
+   shape): bx threads per block along x (a block covers
    bx - 2 columns), h rows per block or strip segment (0 = choose
    automatically: balanced segments of at most 32 rows for warp strips, 64
    for blocks; for warp strips the limit is halved, down to 2 rows, while
@@ -339,7 +351,8 @@ lbm_status lbm_save(lbm_ctx* ctx, const char* path);
    stopped. */
 lbm_status lbm_load(lbm_ctx* ctx, const char* path);
 
-/* Times lbm_step over `steps` steps for a fixed list of launch shapes
+/* (An implementation call; the paper has no counterpart.)  Times lbm_step
+   over `steps` steps for a fixed list of launch shapes
    (pipeline, block width, rows per block) on the context's own lattices and
    keeps the fastest.  The state and the step counter are restored after
    every trial, so the call changes nothing but the launch shape; results do

@@ -525,10 +525,13 @@ def _brute_force_step(f, p, solid, gw, fsi):
     lam = np.array([one / p["tau_rho"], one / p["tau_e"], one / p["tau_zeta"], one / p["tau_j"],
                     one / p["tau_q"], one / p["tau_j"], one / p["tau_q"], 1 / tnu, 1 / tnu])
     vF, Fm2 = vx * Fx + vy * Fy, Fmx ** 2 + Fmy ** 2
-    S = np.array([0 * rho,
-                  6 * vF + 12 * p["sigma"] * Fm2 / (psi ** 2 * (p["tau_e"] - 0.5)),
-                  -6 * vF - 12 * p["sigma"] * Fm2 / (psi ** 2 * (p["tau_zeta"] - 0.5)),
-                  Fx, -Fx, Fy, -Fy, 2 * (vx * Fx - vy * Fy), vx * Fy + vy * Fx])
+    # solid nodes under the ZERO ghost have psi = 0: their collision is never
+    # read (pulls from solid take the bounced population of the fluid node)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        S = np.array([0 * rho,
+                      6 * vF + 12 * p["sigma"] * Fm2 / (psi ** 2 * (p["tau_e"] - 0.5)),
+                      -6 * vF - 12 * p["sigma"] * Fm2 / (psi ** 2 * (p["tau_zeta"] - 0.5)),
+                      Fx, -Fx, Fy, -Fy, 2 * (vx * Fx - vy * Fy), vx * Fy + vy * Fx])
     m = np.tensordot(M, f, 1)
     fs = np.tensordot(np.linalg.inv(M), m - lam * (m - meq) + (1 - lam / 2) * S, 1)
     out = np.empty_like(f)
