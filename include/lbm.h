@@ -325,9 +325,13 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, long T, double theta_target, double y_w, do
    rows with loads prefetched into registers; 2 = independent warps, each
    marching up a 30-column strip (no block barriers),
    with FP32 storage two rows at a time on the paired FP32 instructions;
-   3 = the same warp strips one row at a time; 8 or 16 = blocks marching up rows with a TMA ring of that many source rows
-   in shared memory (FP32 storage, every lattice width a multiple of 4);
-   0 = automatic (warp strips, as 2).  Results do not depend on any of these
+   3 = the same warp strips one row at a time; 4 = independent warps, each
+   marching up a 60-column strip one row at a time with two columns per lane
+   on the paired FP32 instructions (FP32 storage, every lattice width a
+   multiple of 4, not persistent; otherwise as 2); 8 or 16 = blocks marching
+   up rows with a TMA ring of that many source rows in shared memory (FP32
+   storage, every lattice width a multiple of 4); 0 = automatic (4 where it
+   applies, else warp strips as 2).  Results do not depend on any of these
    choices.  A persistent launch needs one parameter set across the batch
    (LBM_ERR_ARG otherwise). */
 lbm_status lbm_set_launch(lbm_ctx* ctx, int bx, int h, int persistent, int graph, int stages);
@@ -336,7 +340,8 @@ lbm_status lbm_set_launch(lbm_ctx* ctx, int bx, int h, int persistent, int graph
    has no counterpart): threads per block, and the pipeline as a code: 1 =
    block rows, 2 = FP32 warp strips two rows per lane, 3 = warp strips one
    row per lane (FP64 and FP32 with FP64 density, stages 3, and every
-   persistent warp-strip launch), 8 or 16 = block rows with a TMA ring; and
+   persistent warp-strip launch), 4 = FP32 warp strips two columns per lane,
+   8 or 16 = block rows with a TMA ring; and
    the persistent flag as set.  Outputs may be NULL. */
 lbm_status lbm_get_launch(const lbm_ctx* ctx, int* bx, int* pipeline, int* persistent);
 

@@ -502,9 +502,16 @@ static lbm_status build_items(lbm_ctx* c) {
   c->graphs.clear();
   // block rows: a block of bx threads covers bx - 2 columns (its two edge
   // lanes evaluate the halo columns); warp strips: each warp covers 30
-  const bool warp_mode = c->stages == 0 || c->stages == 2 || c->stages == 3;
-  // FP32 storage in warp strips: two rows per lane unless one is asked for
-  const bool two_rows = warp_mode && c->stages != 3 && c->prec == LBM_FP32_SHIFTED;
+  // FP32 storage: strips with two columns per lane where every lattice
+  // width is a multiple of 4 (automatic, or stages 4), else two rows per
+  // lane unless one is asked for; a persistent launch takes one row per lane
+  bool cols_ok = c->prec == LBM_FP32_SHIFTED && !c->persistent;
+  for (auto& I : c->inst) cols_ok = cols_ok && (I.nx % 4 == 0);
+  const bool cols_mode = cols_ok && (c->stages == 0 || c->stages == 4);
+  const bool warp_mode = cols_mode || c->stages == 0 || c->stages == 2 || c->stages == 3 ||
+                         c->stages == 4;
+  const bool two_rows = warp_mode && !cols_mode && c->stages != 3 &&
+                        c->prec == LBM_FP32_SHIFTED;
   int bx = c->bx;
   if (bx <= 0) {
     // widest instance decides; whole rows up to 512 threads, else 256-wide strips
@@ -515,9 +522,9 @@ static lbm_status build_items(lbm_ctx* c) {
   }
   // warp strips: 8 warps per block; 4 for two rows per lane (128 registers
   // a thread: four blocks, 16 warps per SM)
-  if (warp_mode && c->bx <= 0) bx = two_rows ? 128 : 256;
+  if (warp_mode && c->bx <= 0) bx = cols_mode ? 64 : (two_rows ? 128 : 256);
   bx = std::max(32, std::min(warp_mode ? 256 : 512, ((bx + 31) / 32) * 32));
-  const int cols = warp_mode ? 30 : bx - 2;
+  const int cols = cols_mode ? 60 : (warp_mode ? 30 : bx - 2);
   // parameter classes, in order of first appearance
   c->cls.clear();
   c->cls_beg.clear();
@@ -573,6 +580,14 @@ static lbm_status build_items(lbm_ctx* c) {
       // many strips as possible but no more than one per resident warp
       while (hmax < maxny && count(hmax) > slots) hmax *= 2;
       while (hmax > 2 && count(hmax / 2) <= slots) hmax /= 2;
+    } else if (cols_mode) {
+      // the tallest segments that still give 3.5 waves of strips.  Fewer
+      // waves leave SMs idle at the end of the step; shorter segments spend
+      // more on their two halo rows; one wave of long runs of rows per warp
+      // touches the whole batch at once and ran at two thirds of the rate
+      // (sweep of 72 400x200 lattices: 12-row segments, 3.5 waves, beat 25-
+      // to 29-row ones by 8%); a batch too small for that takes 2-row segments
+      while (hmax > 2 && 2 * count(hmax) < 7 * slots) --hmax;
     } else {
       while (hmax > 2 && count(hmax) < 2 * slots) hmax = std::max(2, hmax / 2);
     }
@@ -649,8 +664,9 @@ static lbm_status build_items(lbm_ctx* c) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   while (S >= 8 && tma_smem_bytes(bx, S) > (size_t)optin) S /= 2;
-  c->stages_used = warp_mode ? (c->stages == 3 ? PIPE_WARP1 : PIPE_WARP)
-                              : ((tma_ok && c->stages != 1 && S >= 8) ? S : 0);
+  c->stages_used = cols_mode   ? PIPE_COLS
+                   : warp_mode ? (c->stages == 3 ? PIPE_WARP1 : PIPE_WARP)
+                               : ((tma_ok && c->stages != 1 && S >= 8) ? S : 0);
   return LBM_OK;
 }
 
@@ -1150,10 +1166,10 @@ extern "C" lbm_status lbm_set_launch(lbm_ctx* c, int bx, int h, int persistent, 
                                       int stages) {
   if (!c) return fail(LBM_ERR_ARG, "ctx is NULL");
   if (bx < 0 || bx > 512 || h < 0) return fail(LBM_ERR_ARG, "need 0 <= bx <= 512 and h >= 0");
-  if (!(stages >= 0 && stages <= 3) && stages != 8 && stages != 16)
+  if (!(stages >= 0 && stages <= 4) && stages != 8 && stages != 16)
     return fail(LBM_ERR_ARG, "stages must be 0 (automatic), 1 (block rows), 2 (warp strips), "
-                             "3 (warp strips, one row per lane), "
-                             "8 or 16 (TMA ring)");
+                             "3 (warp strips, one row per lane), 4 (warp strips, two columns "
+                             "per lane), 8 or 16 (TMA ring)");
   CK(cudaStreamSynchronize(c->stream));
   c->bx = bx;
   c->h = h;
@@ -1169,6 +1185,7 @@ extern "C" lbm_status lbm_get_launch(const lbm_ctx* c, int* bx, int* pipeline,
   int code = c->stages_used;
   if (code == PIPE_BLOCK) code = 1;
   else if (code == PIPE_WARP) code = c->prec == LBM_FP32_SHIFTED ? 2 : 3;
+  else if (code == PIPE_COLS) code = 4;
   if (c->persistent && is_warp_pipe(c->stages_used)) code = 3;  // one row per lane
   if (bx) *bx = c->bx_used;
   if (pipeline) *pipeline = code;
@@ -1704,9 +1721,12 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, int steps, int* bx_out, int* h_ou
   struct Cand {
     int bx, h, stages;
   };
-  // warp strips (two rows per lane with FP32 storage: even h), warp strips
-  // one row per lane, block rows, TMA block rows
-  std::vector<Cand> cands = {{128, 0, 2},  {128, 4, 2},  {128, 8, 2},  {128, 16, 2},
+  // FP32 warp strips with two columns per lane, warp strips (two rows per
+  // lane with FP32 storage: even h), warp strips one row per lane, block
+  // rows, TMA block rows
+  std::vector<Cand> cands = {{128, 0, 4},  {128, 8, 4},  {128, 16, 4}, {128, 32, 4},
+                             {64, 0, 4},   {256, 0, 4},
+                             {128, 0, 2},  {128, 4, 2},  {128, 8, 2},  {128, 16, 2},
                              {128, 24, 2}, {128, 32, 2}, {64, 32, 2},  {256, 32, 2},
                              {256, 0, 3},  {256, 8, 3},  {256, 25, 3}, {256, 32, 3}, {128, 32, 3},
                              {224, 32, 1}, {224, 50, 1}, {416, 50, 1}, {224, 50, 8},
@@ -1725,6 +1745,7 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, int steps, int* bx_out, int* h_ou
     c->stages = q.stages;
     if (build_items(c) != LBM_OK) continue;
     if (q.stages >= 8 && c->stages_used < 8) continue;  // TMA not applicable here
+    if (q.stages == 4 && c->stages_used != PIPE_COLS) continue;  // widths not multiples of 4
     put_back();
     if (lbm_step(c, 2) != LBM_OK) continue;
     cudaEventRecord(e0, c->stream);

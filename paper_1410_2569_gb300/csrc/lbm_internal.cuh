@@ -127,9 +127,10 @@ __device__ __forceinline__ constexpr bool in_bounds(long long, long long, int*) 
 
 // step pipelines (launch_step's `stages` argument): block rows with register
 // prefetch, warp strips (two rows per lane with FP32 storage, one otherwise),
-// warp strips with one row per lane, or block rows with a TMA ring of 8 / 16
-// stages
-enum : int { PIPE_BLOCK = 0, PIPE_WARP = 2, PIPE_WARP1 = 3 };
+// warp strips with one row per lane, FP32 warp strips with two columns per
+// lane (every lattice width a multiple of 4), or block rows with a TMA ring
+// of 8 / 16 stages
+enum : int { PIPE_BLOCK = 0, PIPE_WARP = 2, PIPE_WARP1 = 3, PIPE_COLS = 4 };
 inline bool is_warp_pipe(int S) { return S == PIPE_WARP || S == PIPE_WARP1; }
 
 // D2Q9 weights of the equilibrium

@@ -33,6 +33,10 @@ CASES = [
     (33, 12, "fp64", dict(persistent=True, stages=1, h=3), {}, "flat"),
     (38, 24, "fp32", dict(h=3), dict(wall="bb", ghost="mean"), "pillars"),
     (9, 7, "fp32", dict(h=1), dict(ghost="mirror"), "flat"),
+    (36, 20, "fp32", dict(stages=4, h=3), {}, "flat"),
+    (68, 9, "fp32", dict(stages=4, h=1, bx=64), {}, "flat"),
+    (12, 10, "fp32", dict(stages=4, h=2), dict(ghost="mirror"), "flat"),
+    (40, 24, "fp32", dict(stages=4, h=5), dict(wall="bb", ghost="mean"), "pillars"),
 ]
 STEPS = 40
 

@@ -142,6 +142,42 @@ def test_tma_pipeline_bitwise_equal_to_register_pipeline(cuda, prec, launch):
         assert np.array_equal(got.populations(i), ref.populations(i)), (i, launch)
 
 
+@pytest.mark.parametrize("launch", [dict(), dict(stages=4), dict(stages=4, h=1),
+                                    dict(stages=4, bx=64, h=5), dict(stages=4, bx=256, h=3),
+                                    dict(stages=4, bx=32, h=2), dict(stages=4, h=7, graph=True)])
+def test_column_pair_strips_bitwise(cuda, launch):
+    """FP32 warp strips with two columns per lane (every width a multiple of
+    4; the automatic choice there) against the block rows, bit for bit, on
+    ragged strips (36 .. 252 columns) and segment heights 1 .. 7."""
+    specs = _batch_specs_w4("fp32")
+    ref = _run_batch(specs, 130, dict(stages=1))
+    got = _run_batch(specs, 130, launch)
+    assert got.launch()["pipeline"] == 4
+    for i in range(len(specs)):
+        assert np.array_equal(got.populations(i), ref.populations(i)), (i, launch)
+
+
+def test_column_pairs_need_widths_multiple_of_4(cuda):
+    """A batch with a width that is not a multiple of 4 keeps the two-row
+    strips, asked for or not."""
+    b = _run_batch(_batch_specs("fp32"), 2)
+    assert b.launch()["pipeline"] == 2
+    b.set_launch(stages=4)
+    assert b.launch()["pipeline"] == 2
+
+
+@pytest.mark.parametrize("ghost", ["skip", "mean"])
+def test_column_pair_strips_pillars(cuda, ghost):
+    nx, ny = 92, 60
+    solid = inputs.pillars(nx, ny, height=10, width=6, gap=3)
+    drop = (45.0, 30.0, 15.0, 2.0)
+    a = run_gpu(nx, ny, 300, "modified", 0.3, solid, drop, launch=dict(stages=1), prec="fp32",
+                wall="bb", ghost=ghost)
+    b = run_gpu(nx, ny, 300, "modified", 0.3, solid, drop, launch=dict(stages=4, h=9),
+                prec="fp32", wall="bb", ghost=ghost)
+    assert np.array_equal(a.populations(), b.populations())
+
+
 def test_tma_pipeline_bounce_back_pillars(cuda):
     nx, ny = 92, 60
     solid = inputs.pillars(nx, ny, height=10, width=6, gap=3)

@@ -17,15 +17,17 @@ RATIO1 = dict(tau_nu_L=1.1, tau_nu_V=1.1)
 RATIO2 = dict(tau_nu_L=1.1, tau_nu_V=1.7)
 
 
-def _mixed_specs(prec):
-    # two viscosity ratios (same launch), and a different sigma (own launch)
+def _mixed_specs(prec, w4=False):
+    # two viscosity ratios (same launch), and a different sigma (own launch);
+    # w4: every width a multiple of 4 (the FP32 column-pair strips apply)
     ratio1, ratio10, other = RATIO1, RATIO2, dict(sigma=0.1)
+    widths = (96, 72, 64, 36, 132) if w4 else (96, 70, 64, 33, 130)
     specs = []
-    for fsi, gw, nx, ny, over in [("modified", 0.2, 96, 48, ratio1),
-                                  ("density", 0.05, 70, 41, ratio10),
-                                  ("psi", -0.9, 64, 40, other),
-                                  ("modified", -0.1, 33, 27, ratio10),
-                                  ("density", -0.05, 130, 36, ratio1)]:
+    for (fsi, gw, ny, over), nx in zip([("modified", 0.2, 48, ratio1),
+                                        ("density", 0.05, 41, ratio10),
+                                        ("psi", -0.9, 40, other),
+                                        ("modified", -0.1, 27, ratio10),
+                                        ("density", -0.05, 36, ratio1)], widths):
         specs.append(dict(nx=nx, ny=ny, params=gpu_params(prec=prec, **over),
                           solid=inputs.flat_walls(nx, ny), fsi=fsi, gw=gw,
                           drop=(nx / 2, 0.5, ny / 3, 3.0), over=over))
@@ -51,6 +53,20 @@ def test_mixed_batch_matches_instances_alone(cuda, prec, launch):
     for i, s in enumerate(specs):
         alone = run_gpu(s["nx"], s["ny"], 120, s["fsi"], s["gw"], s["solid"], s["drop"],
                         launch=dict(stages=1), prec=prec, **s["over"])
+        assert np.array_equal(b.populations(i), alone.populations()), (i, launch)
+
+
+@pytest.mark.parametrize("launch", [None, dict(stages=4, h=5), dict(stages=4, bx=64, h=3),
+                                    dict(stages=4, graph=True)])
+def test_mixed_batch_column_pairs(cuda, launch):
+    """The column-pair strips on a batch of two parameter classes and two
+    viscosity ratios, instance by instance against block rows alone."""
+    specs = _mixed_specs("fp32", w4=True)
+    b = _run(specs, 120, launch)
+    assert b.launch()["pipeline"] == 4
+    for i, s in enumerate(specs):
+        alone = run_gpu(s["nx"], s["ny"], 120, s["fsi"], s["gw"], s["solid"], s["drop"],
+                        launch=dict(stages=1), prec="fp32", **s["over"])
         assert np.array_equal(b.populations(i), alone.populations()), (i, launch)
 
 
