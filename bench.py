@@ -439,10 +439,11 @@ def batched_uneven(stream, steps=1000):
     """The batched workload: 64 lattices of seeded log-uniform sizes (128x64
     to 512x256), random interaction and G_w per lattice, droplets of radius
     ny/4, FP32 storage.  MLUPS (all nodes) over `steps` steps for each launch
-    mode: warp strips one launch per step; the same in a CUDA graph of
+    mode: warp strips one launch per step (the FP32 column-pair strips:
+    every width here is a multiple of 8); the same in a CUDA graph of
     `steps` launches; one persistent cooperative launch per `steps` steps
-    captured in a graph, block rows with a grid barrier per step or warp
-    strips (one row per lane) waiting on their neighbours; the shape
+    captured in a graph, block rows with a grid barrier per step or the
+    column-pair strips each waiting on its neighbours; the shape
     lbm_autotune picks."""
     import paper_1410_2569_gb300 as lbm
     from paper_1410_2569_gb300 import inputs

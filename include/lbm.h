@@ -315,10 +315,11 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, long T, double theta_target, double y_w, do
    persistent warp strips it is the height that gives the most strips not
    exceeding one per resident warp),
    persistent = 1 runs all n steps in one cooperative launch: block
-   pipelines with a bounded grid barrier between steps, warp strips one row
-   per lane with no barrier (a strip starts a step once the strips within
-   four nodes of it have finished the previous one; every wait is bounded
-   and a time-out returns LBM_ERR_TIMEOUT at the next synchronising call),
+   pipelines with a bounded grid barrier between steps, warp strips (the
+   FP32 column pairs of stages 4 where they apply, else one row per lane)
+   with no barrier (a strip starts a step once the strips within four nodes
+   of it have finished the previous one; every wait is bounded and a
+   time-out returns LBM_ERR_TIMEOUT at the next synchronising call),
    graph = 1 captures the n per-step launches (or
    the one persistent launch) in a CUDA graph, reused for every later call
    with the same n.  stages selects the step pipeline: 1 = blocks marching up
@@ -328,7 +329,7 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, long T, double theta_target, double y_w, do
    3 = the same warp strips one row at a time; 4 = independent warps, each
    marching up a 60-column strip one row at a time with two columns per lane
    on the paired FP32 instructions (FP32 storage, every lattice width a
-   multiple of 4, not persistent; otherwise as 2); 8 or 16 = blocks marching
+   multiple of 4; otherwise as 2); 8 or 16 = blocks marching
    up rows with a TMA ring of that many source rows in shared memory (FP32
    storage, every lattice width a multiple of 4); 0 = automatic (4 where it
    applies, else warp strips as 2).  Results do not depend on any of these
@@ -339,8 +340,9 @@ lbm_status lbm_set_launch(lbm_ctx* ctx, int bx, int h, int persistent, int graph
 /* The launch shape lbm_step uses now (an implementation detail; the paper
    has no counterpart): threads per block, and the pipeline as a code: 1 =
    block rows, 2 = FP32 warp strips two rows per lane, 3 = warp strips one
-   row per lane (FP64 and FP32 with FP64 density, stages 3, and every
-   persistent warp-strip launch), 4 = FP32 warp strips two columns per lane,
+   row per lane (FP64 and FP32 with FP64 density, stages 3, and the
+   persistent launch of the warp strips of stages 2), 4 = FP32 warp strips
+   two columns per lane (per step or persistent),
    8 or 16 = block rows with a TMA ring; and
    the persistent flag as set.  Outputs may be NULL. */
 lbm_status lbm_get_launch(const lbm_ctx* ctx, int* bx, int* pipeline, int* persistent);

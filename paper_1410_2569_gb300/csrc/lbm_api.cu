@@ -503,9 +503,10 @@ static lbm_status build_items(lbm_ctx* c) {
   // block rows: a block of bx threads covers bx - 2 columns (its two edge
   // lanes evaluate the halo columns); warp strips: each warp covers 30
   // FP32 storage: strips with two columns per lane where every lattice
-  // width is a multiple of 4 (automatic, or stages 4), else two rows per
-  // lane unless one is asked for; a persistent launch takes one row per lane
-  bool cols_ok = c->prec == LBM_FP32_SHIFTED && !c->persistent;
+  // width is a multiple of 4 (automatic, or stages 4; per-step or
+  // persistent), else two rows per lane unless one is asked for (a
+  // persistent launch of those takes one row per lane)
+  bool cols_ok = c->prec == LBM_FP32_SHIFTED;
   for (auto& I : c->inst) cols_ok = cols_ok && (I.nx % 4 == 0);
   const bool cols_mode = cols_ok && (c->stages == 0 || c->stages == 4);
   const bool warp_mode = cols_mode || c->stages == 0 || c->stages == 2 || c->stages == 3 ||
@@ -891,9 +892,10 @@ static cudaError_t launch_one_step(lbm_ctx* c, int parity, cudaStream_t s) {
 static cudaError_t launch_persistent(lbm_ctx* c, long n, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(c->d_barrier + 1, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  if (is_warp_pipe(c->stages_used))
+  if (is_warp_pipe(c->stages_used) || c->stages_used == PIPE_COLS)
     return launch_step_dataflow(c->prec, c->cls[0], c->d_desc, c->d_items, c->d_nbr_off,
-                                c->d_nbr, c->n_items, c->parity, n, c->bx_used, c->d_done,
+                                c->d_nbr, c->n_items, c->parity, n, c->bx_used,
+                                c->stages_used, c->d_done,
                                 (int*)(c->d_barrier + 1), s);
   return launch_step_persistent(c->prec, c->cls[0], c->d_desc, c->d_items, c->n_items, c->parity,
                                 n, c->bx_used, c->stages_used, c->d_barrier, s);

@@ -177,13 +177,16 @@ cudaError_t launch_step_persistent(int prec, const PhysDesc& ph, const InstDesc*
                                    int n_items, int parity0, long n_steps, int bx, int stages,
                                    unsigned* d_barrier, cudaStream_t s);
 int persistent_max_blocks(int prec, int bx, int stages);
-// warp strips, one row per lane, for n steps in one cooperative launch: item
+// warp strips (one row per lane, or the FP32 column pairs) for n steps in one
+// cooperative launch: item
 // i of a step starts when the items nbr[nbr_off[i] .. nbr_off[i+1]) have
 // finished the previous step (done: n_items counters, zeroed here first;
 // err: the kernel's error word, ERR_TIMEOUT when a wait gave up)
+// pipe: PIPE_COLS for the FP32 column-pair strips (60-column items), else
+// one row per lane (30-column items)
 cudaError_t launch_step_dataflow(int prec, const PhysDesc& ph, const InstDesc* d_inst,
                                  const WorkItem* d_items, const int* d_nbr_off, const int* d_nbr,
-                                 int n_items, int parity0, long n_steps, int bx,
+                                 int n_items, int parity0, long n_steps, int bx, int pipe,
                                  unsigned* d_done, int* d_err, cudaStream_t s);
 cudaError_t launch_barrier_selftest(unsigned* d_bar, int* d_err, double seconds, cudaStream_t s);
 cudaError_t launch_init(int prec, const InstDesc& h_inst, const InstDesc* d_inst, int parity,

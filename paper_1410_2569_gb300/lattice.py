@@ -145,20 +145,22 @@ class Lattice:
         check(self._L.lbm_sync(self._h))
 
     def set_launch(self, bx=0, h=0, persistent=False, graph=False, stages=0):
-        """Launch shape and pipeline of step() (lbm_set_launch): stages 0/2 warp
-        strips (two rows per lane with FP32 storage), 3 warp strips one row per
-        lane, 1 block rows, 8/16 block rows with a TMA ring.  persistent=True
-        runs all steps of a call in one cooperative launch (warp strips one
-        row per lane, each waiting only on its neighbours; block rows with a
-        grid barrier); graph=True replays the launches of a call from a CUDA
-        graph."""
+        """Launch shape and pipeline of step() (lbm_set_launch): stages 0
+        automatic, 4 FP32 warp strips with two columns per lane (every width
+        a multiple of 4; the automatic choice there), 2 warp strips (two rows
+        per lane with FP32 storage), 3 warp strips one row per lane, 1 block
+        rows, 8/16 block rows with a TMA ring.  persistent=True runs all
+        steps of a call in one cooperative launch (warp strips, each waiting
+        only on its neighbours; block rows with a grid barrier); graph=True
+        replays the launches of a call from a CUDA graph."""
         check(self._L.lbm_set_launch(self._h, int(bx), int(h), int(persistent), int(graph),
                                      int(stages)))
 
     def launch(self):
         """The launch shape in use (lbm_get_launch): dict(bx, pipeline,
-        persistent); pipeline 2 is the FP32 warp strips with two rows per
-        lane, 3 the warp strips with one row per lane, 1 the block rows."""
+        persistent); pipeline 4 is the FP32 warp strips with two columns
+        per lane, 2 the FP32 warp strips with two rows per lane, 3 the warp
+        strips with one row per lane, 1 the block rows."""
         bx, pl, pe = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(self._L.lbm_get_launch(self._h, ctypes.byref(bx), ctypes.byref(pl),
                                           ctypes.byref(pe)))

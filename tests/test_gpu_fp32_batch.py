@@ -144,11 +144,15 @@ def test_tma_pipeline_bitwise_equal_to_register_pipeline(cuda, prec, launch):
 
 @pytest.mark.parametrize("launch", [dict(), dict(stages=4), dict(stages=4, h=1),
                                     dict(stages=4, bx=64, h=5), dict(stages=4, bx=256, h=3),
-                                    dict(stages=4, bx=32, h=2), dict(stages=4, h=7, graph=True)])
+                                    dict(stages=4, bx=32, h=2), dict(stages=4, h=7, graph=True),
+                                    dict(persistent=True), dict(persistent=True, h=5),
+                                    dict(persistent=True, bx=128, h=2),
+                                    dict(stages=4, persistent=True, graph=True)])
 def test_column_pair_strips_bitwise(cuda, launch):
     """FP32 warp strips with two columns per lane (every width a multiple of
-    4; the automatic choice there) against the block rows, bit for bit, on
-    ragged strips (36 .. 252 columns) and segment heights 1 .. 7."""
+    4; the automatic choice there), launched per step or all steps in one
+    persistent launch, against the block rows, bit for bit, on ragged strips
+    (36 .. 252 columns) and segment heights 1 .. 7."""
     specs = _batch_specs_w4("fp32")
     ref = _run_batch(specs, 130, dict(stages=1))
     got = _run_batch(specs, 130, launch)

@@ -80,7 +80,8 @@ def test_autotune_changes_only_the_launch_shape(cuda):
 @pytest.mark.parametrize("launch", [dict(stages=1, persistent=True, graph=True),
                                     dict(stages=8, persistent=True, graph=True),
                                     dict(stages=2, persistent=True, graph=True),
-                                    dict(stages=3, bx=64, h=5, persistent=True, graph=True)])
+                                    dict(stages=3, bx=64, h=5, persistent=True, graph=True),
+                                    dict(stages=4, persistent=True, graph=True)])
 def test_graph_captured_persistent_launch(cuda, launch):
     specs = _specs("fp32", widths=((64, 40), (132, 48), (96, 70), (36, 20), (252, 36)))
     ref = _make(specs)
@@ -93,13 +94,14 @@ def test_graph_captured_persistent_launch(cuda, launch):
 
 
 @pytest.mark.parametrize("launch", [dict(stages=1, persistent=True, graph=True),
-                                    dict(stages=2, persistent=True, graph=True)])
+                                    dict(stages=2, persistent=True, graph=True),
+                                    dict(stages=4, persistent=True, graph=True)])
 def test_batched_uneven_lattices(cuda, launch):
     """64 lattices, widths 128..512 drawn log-uniform from a seed, random
     interaction and G_w, radius 0.25 ny, FP32 populations with compensated
     density; one persistent launch per 100 steps replayed from a CUDA graph
-    (block rows with a grid barrier, or warp strips waiting on their
-    neighbours)."""
+    (block rows with a grid barrier, or warp strips, one row or two
+    columns per lane, waiting on their neighbours)."""
     insts = inputs.batch_instances(64, seed=0)
     specs = []
     for d in insts:

@@ -80,25 +80,32 @@ def _ctx_lists(lat):
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("shape", [dict(), dict(h=3), dict(h=2, bx=64)])
-def test_context_lists_of_a_persistent_batch_match_brute_force(cuda, prec, shape):
+@pytest.mark.parametrize("widths", ["any", "w4"])
+def test_context_lists_of_a_persistent_batch_match_brute_force(cuda, prec, shape, widths):
     """The items and dependency lists a persistent warp-strip batch actually
     runs with (lbm_get_work_items): several instances of uneven sizes (odd
-    heights among them), the automatic segment heights and fixed ones.  Item
-    j is listed for item i exactly when both belong to one instance and a
-    node of j lies within 4 nodes of one of i along x and along y
-    (periodic); items of other instances are never listed."""
+    heights among them), the automatic segment heights and fixed ones; with
+    every width a multiple of 4 the FP32 batch runs the column-pair strips
+    (60-column items), otherwise the one-row strips (30 columns).  Item j is
+    listed for item i exactly when both belong to one instance and a node of
+    j lies within 4 nodes of one of i along x and along y (periodic); items
+    of other instances are never listed."""
     from paper_1410_2569_gb300 import inputs
-    shapes = [(64, 40), (130, 48), (96, 70), (33, 21), (257, 37)]
+    shapes = ([(64, 40), (130, 48), (96, 70), (33, 21), (257, 37)] if widths == "any" else
+              [(64, 40), (132, 48), (96, 70), (36, 21), (252, 37)])
     specs = [dict(nx=nx, ny=ny, params=lbm.default_params(prec=prec),
                   solid=inputs.flat_walls(nx, ny), fsi="modified", gw=0.1) for nx, ny in shapes]
     lat = lbm.Lattice(specs)
     lat.set_launch(persistent=True, **shape)
+    pipe = lat.launch()["pipeline"]
+    assert pipe == (4 if (prec == "fp32" and widths == "w4") else 3)
+    W = 60 if pipe == 4 else 30
     items, lists = _ctx_lists(lat)
     for k, (nx, ny) in enumerate(shapes):
         cover = np.zeros((ny, nx), int)
         for inst, x0, y0, y1 in items:
             if inst == k:
-                cover[y0:y1, x0:min(nx, x0 + 30)] += 1
+                cover[y0:y1, x0:min(nx, x0 + W)] += 1
         assert (cover == 1).all(), k
     heights = {int(y1 - y0) for _, _, y0, y1 in items}
     assert len(heights) > 1  # segments of different heights (odd ny, short last segments)
@@ -107,7 +114,7 @@ def test_context_lists_of_a_persistent_batch_match_brute_force(cuda, prec, shape
         listed = set(lists[i])
         assert len(listed) == len(lists[i]) and i in listed
         for j, (kj, u0, v0, v1) in enumerate(items):
-            near = (kj == k and _gap(x0, min(nx, x0 + 30), u0, min(nx, u0 + 30), nx) <= 4 and
+            near = (kj == k and _gap(x0, min(nx, x0 + W), u0, min(nx, u0 + W), nx) <= 4 and
                     _gap(y0, y1, v0, v1, ny) <= 4)
             assert (j in listed) == near, (i, j)
     # one launch per step: the same items, no lists
