@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <map>
 #include <string>
+#include <functional>
 #include <tuple>
 #include <vector>
 
@@ -1403,12 +1404,17 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, long T, double theta_target, doubl
   // checkpoints every k steps: the library state (f*, F at walls) and parity
   const long k = (long)ceil(sqrt((double)T));
   const long nck = (T + k - 1) / k;
-  DevBuf ck, seg, segrp, lamA, lamB, grad, scr;
+  DevBuf ck, seg[2], segrp[2], lamA, lamB, grad, scr;
   const size_t ck_one = (fN + 2 * N) * sizeof(double);
   CK(cudaMalloc(&ck.p, nck * ck_one));
-  // one segment of recomputed forward states: f(t), and rho(t), psi(t)
-  CK(cudaMalloc(&seg.p, (size_t)k * fN * sizeof(double)));
-  CK(cudaMalloc(&segrp.p, (size_t)k * 2 * N * sizeof(double)));
+  // recomputed forward states of a segment, f(t) and rho(t), psi(t), twice:
+  // the reverse sweep of one segment reads one buffer while the next
+  // segment is recomputed into the other
+  const int nbuf = nck > 1 ? 2 : 1;
+  for (int b = 0; b < nbuf; ++b) {
+    CK(cudaMalloc(&seg[b].p, (size_t)k * fN * sizeof(double)));
+    CK(cudaMalloc(&segrp[b].p, (size_t)k * 2 * N * sizeof(double)));
+  }
   CK(cudaMalloc(&lamA.p, fN * sizeof(double)));
   CK(cudaMalloc(&lamB.p, fN * sizeof(double)));
   CK(cudaMalloc(&grad.p, N * sizeof(double)));
@@ -1487,69 +1493,114 @@ extern "C" lbm_status lbm_adjoint(lbm_ctx* c, long T, double theta_target, doubl
                      c->stream));
   double* lam_next = (double*)lamA.p;
   double* lam_cur = (double*)lamB.p;
-  // One segment: recompute f(t) of its len steps from the restored
-  // checkpoint, then len reverse steps.  The launches of a segment are
-  // captured once per (len, starting parity, which buffer holds lam) and
-  // replayed from a CUDA graph: the kernels of a 256 x 128 lattice last a
-  // few microseconds each, so launch gaps would otherwise dominate.
-  auto enqueue_segment = [&](long len, int p0, double* ln, double* lc,
-                             cudaStream_t s) -> cudaError_t {
+  // A segment: the forward states f(t) of its len steps recomputed from the
+  // restored checkpoint (context stream), then its len reverse steps (a
+  // stream of their own).  The reverse sweep of segment ci runs while
+  // segment ci - 1 is recomputed into the other buffer: on a small lattice
+  // neither fills the GPU.  Each part is captured once per (len, parity or
+  // lam orientation, buffer) and replayed from a CUDA graph: the kernels of
+  // a 256 x 128 lattice last a few microseconds each.
+  auto enqueue_recompute = [&](long len, int p0, int b, cudaStream_t s) -> cudaError_t {
     cudaError_t e = cudaSuccess;
     int par = p0;
     for (long q = 0; q < len && e == cudaSuccess; ++q) {
-      double* fs = (double*)seg.p + q * fN;
-      double* rs = (double*)segrp.p + q * 2 * N;
+      double* fs = (double*)seg[b].p + q * fN;
+      double* rs = (double*)segrp[b].p + q * 2 * N;
       e = launch_macro(c->prec, I.desc, c->d_desc, par, rs, rs + N, nullptr, nullptr, fs, s,
                        false);
       if (e == cudaSuccess) e = launch_one_step(c, par, s);
       par ^= 1;
     }
+    return e;
+  };
+  auto enqueue_reverse = [&](long len, int b, double* ln, double* lc,
+                             cudaStream_t s) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
     for (long q = len - 1; q >= 0 && e == cudaSuccess; --q) {
-      const double* fs = (const double*)seg.p + q * fN;
-      double* rs = (double*)segrp.p + q * 2 * N;
+      const double* fs = (const double*)seg[b].p + q * fN;
+      double* rs = (double*)segrp[b].p + q * 2 * N;
       e = launch_adjoint_step(I.desc, c->d_desc, fs, rs, rs + N, ln, lc, (double*)grad.p, S, s);
       std::swap(ln, lc);
     }
     return e;
   };
-  std::map<std::tuple<long, int, int>, cudaGraphExec_t> seg_graphs;
-  cudaStream_t cap = nullptr;
+  std::map<std::tuple<int, long, int, int>, cudaGraphExec_t> graphs;
+  cudaStream_t cap = nullptr, rev = nullptr;
+  cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&rev, cudaStreamNonBlocking);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaEventCreateWithFlags(&ev_rec[b], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_rev[b], cudaEventDisableTiming);
+  }
   auto release = [&]() {
+    if (rev) cudaStreamSynchronize(rev);
     cudaStreamSynchronize(c->stream);  // no replay still pending
-    for (auto& kv : seg_graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    for (int b = 0; b < 2; ++b) {
+      if (ev_rec[b]) cudaEventDestroy(ev_rec[b]);
+      if (ev_rev[b]) cudaEventDestroy(ev_rev[b]);
+    }
+    if (rev) cudaStreamDestroy(rev);
     if (cap) cudaStreamDestroy(cap);
   };
-  for (long ci = nck - 1; ci >= 0; --ci) {
-    const long len = std::min(k, T - ci * k);
-    if ((st = restore(ci)) != LBM_OK) {
-      release();
-      return st;
-    }
-    const auto key = std::make_tuple(len, c->parity, lam_next == (double*)lamA.p ? 0 : 1);
-    auto it = seg_graphs.find(key);
-    cudaError_t e = cudaSuccess;
-    if (it == seg_graphs.end()) {
-      if (!cap) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  // replay the graph of `key`, capturing it first with `fill`
+  auto replay = [&](const std::tuple<int, long, int, int>& key, cudaStream_t s,
+                    const std::function<cudaError_t(cudaStream_t)>& fill) -> cudaError_t {
+    auto it = graphs.find(key);
+    cudaError_t r = cudaSuccess;
+    if (it == graphs.end()) {
       cudaGraph_t g = nullptr;
-      if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-      if (e == cudaSuccess) {
-        e = enqueue_segment(len, c->parity, lam_next, lam_cur, cap);
-        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
-        if (e == cudaSuccess) e = e2;
+      r = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (r == cudaSuccess) {
+        r = fill(cap);
+        cudaError_t r2 = cudaStreamEndCapture(cap, &g);
+        if (r == cudaSuccess) r = r2;
       }
       cudaGraphExec_t ge = nullptr;
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+      if (r == cudaSuccess) r = cudaGraphInstantiate(&ge, g, 0);
       if (g) cudaGraphDestroy(g);
-      if (e == cudaSuccess) it = seg_graphs.emplace(key, ge).first;
+      if (r != cudaSuccess) return r;
+      it = graphs.emplace(key, ge).first;
     }
-    if (e == cudaSuccess) e = cudaGraphLaunch(it->second, c->stream);
-    if (e != cudaSuccess) {
-      release();
-      c->persistent = saved_persistent;
-      return fail(LBM_ERR_CUDA, "adjoint segment: %s", cudaGetErrorString(e));
-    }
-    c->parity ^= (int)(len & 1);
+    return cudaGraphLaunch(it->second, s);
+  };
+  auto seg_len = [&](long ci) { return std::min(k, T - ci * k); };
+  // recompute segment ci into buffer ci & 1 on the context stream, once the
+  // reverse sweep that last read that buffer is done
+  auto recompute = [&](long ci) -> cudaError_t {
+    const int b = (int)(ci & 1) % nbuf;
+    cudaError_t r = cudaStreamWaitEvent(c->stream, ev_rev[b], 0);
+    if (r != cudaSuccess) return r;
+    if (restore(ci) != LBM_OK) return cudaErrorUnknown;
+    const long len = seg_len(ci);
+    const int p0 = c->parity;
+    r = replay(std::make_tuple(0, len, p0, b), c->stream,
+               [&](cudaStream_t s) { return enqueue_recompute(len, p0, b, s); });
+    if (r == cudaSuccess) r = cudaEventRecord(ev_rec[b], c->stream);
+    return r;
+  };
+  if (e == cudaSuccess) e = recompute(nck - 1);
+  for (long ci = nck - 1; ci >= 0 && e == cudaSuccess; --ci) {
+    const int b = (int)(ci & 1) % nbuf;
+    const long len = seg_len(ci);
+    e = cudaStreamWaitEvent(rev, ev_rec[b], 0);
+    const int orient = lam_next == (double*)lamA.p ? 0 : 1;
+    double *ln = lam_next, *lc = lam_cur;
+    if (e == cudaSuccess)
+      e = replay(std::make_tuple(1, len, orient, b), rev,
+                 [&](cudaStream_t s) { return enqueue_reverse(len, b, ln, lc, s); });
+    if (e == cudaSuccess) e = cudaEventRecord(ev_rev[b], rev);
     if (len & 1) std::swap(lam_next, lam_cur);
+    if (e == cudaSuccess && ci > 0) e = recompute(ci - 1);
+  }
+  // the context stream goes on after the last reverse step
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+    if (ev_rev[b]) e = cudaStreamWaitEvent(c->stream, ev_rev[b], 0);
+  if (e != cudaSuccess) {
+    release();
+    c->persistent = saved_persistent;
+    return fail(LBM_ERR_CUDA, "adjoint segment: %s", cudaGetErrorString(e));
   }
   release();
   // back to the state after the forward pass
