@@ -618,11 +618,58 @@ static lbm_status build_items(lbm_ctx* c) {
       y0 = y1;
     }
   };
+  // column-pair strips launched per step with the automatic height, on a
+  // batch that gives at least 2.5 waves: tall segments of every lattice
+  // first, then about one wave of 4-row segments taken off the top of each
+  // strip, so that the last wave is short and few SMs wait at its end
+  const bool lpt = cols_mode && !c->persistent && c->h <= 0;
   std::vector<WorkItem> items;
   for (int j = 0; j < (int)c->cls.size(); ++j) {
     c->cls_beg.push_back((int)items.size());
-    for (int k = 0; k < (int)c->inst.size(); ++k)
-      if (inst_cls[k] == j) add_items(k, items);
+    bool split = false;
+    int nshort = 0;
+    if (lpt) {
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const long long slots = 16LL * std::max(sms, 1);
+      long long strips_n = 0, items_n = 0;
+      for (int k = 0; k < (int)c->inst.size(); ++k)
+        if (inst_cls[k] == j) {
+          const Inst& I = c->inst[k];
+          const long long ns = (I.nx + cols - 1) / cols;
+          strips_n += ns;
+          items_n += ns * ((I.ny + seg_h(I, hmax) - 1) / seg_h(I, hmax));
+        }
+      nshort = (int)std::max<long long>(1, (slots + strips_n - 1) / std::max(strips_n, 1LL));
+      split = strips_n > 0 && 2 * items_n >= 5 * slots;
+    }
+    if (!split) {
+      for (int k = 0; k < (int)c->inst.size(); ++k)
+        if (inst_cls[k] == j) add_items(k, items);
+    } else {
+      // per strip: the rows below ny - 4 nshort in tall segments (the
+      // automatic count less nshort, at least one), the rest in 4-row ones
+      std::vector<WorkItem> tall, shorts;
+      for (int k = 0; k < (int)c->inst.size(); ++k) {
+        if (inst_cls[k] != j) continue;
+        const Inst& I = c->inst[k];
+        const int ns = std::min(nshort, std::max(0, (I.ny - 4) / 4));
+        const int ytop = I.ny - 4 * ns;
+        const int nseg_auto = (I.ny + seg_h(I, hmax) - 1) / seg_h(I, hmax);
+        const int nt = std::max(1, std::min(ytop, nseg_auto - ns));
+        int y0 = 0;
+        for (int q = 0; q < nt; ++q) {
+          const int u = ytop / nt + (q < ytop % nt ? 1 : 0);
+          for (int x0 = 0; x0 < I.nx; x0 += cols) tall.push_back({k, x0, y0, y0 + u});
+          y0 += u;
+        }
+        for (int q = 0; q < ns; ++q, y0 += 4)
+          for (int x0 = 0; x0 < I.nx; x0 += cols) shorts.push_back({k, x0, y0, y0 + 4});
+      }
+      items.insert(items.end(), tall.begin(), tall.end());
+      items.insert(items.end(), shorts.begin(), shorts.end());
+    }
     c->cls_n.push_back((int)items.size() - c->cls_beg[j]);
   }
   cudaFree(c->d_items);
