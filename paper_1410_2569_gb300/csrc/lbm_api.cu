@@ -85,7 +85,8 @@ struct lbm_ctx {
   // items of class j are [cls_beg[j], cls_beg[j] + cls_n[j]) and go out in
   // one launch with cls[j] as its kernel parameter
   std::vector<PhysDesc> cls;
-  std::vector<int> cls_beg, cls_n;
+  std::vector<int> cls_beg, cls_n, cls_tall;  // cls_tall: items before the short segments
+  bool alt_items = false;  // d_items holds a second, reversed list for odd steps
   // node offsets of the instances in concatenated batch fields: instance k
   // holds [offs[k], offs[k+1]); d_offs is the device copy
   std::vector<long long> offs;
@@ -531,6 +532,7 @@ static lbm_status build_items(lbm_ctx* c) {
   c->cls.clear();
   c->cls_beg.clear();
   c->cls_n.clear();
+  c->cls_tall.clear();
   std::vector<int> inst_cls(c->inst.size());
   for (size_t k = 0; k < c->inst.size(); ++k) {
     const PhysDesc ph = class_key(c->inst[k].desc.ph);
@@ -669,13 +671,31 @@ static lbm_status build_items(lbm_ctx* c) {
       }
       items.insert(items.end(), tall.begin(), tall.end());
       items.insert(items.end(), shorts.begin(), shorts.end());
+      c->cls_tall.push_back((int)tall.size());
     }
+    if ((int)c->cls_tall.size() <= j) c->cls_tall.push_back((int)items.size() - c->cls_beg[j]);
     c->cls_n.push_back((int)items.size() - c->cls_beg[j]);
   }
   cudaFree(c->d_items);
   c->d_items = nullptr;
-  CK(cudaMalloc(&c->d_items, items.size() * sizeof(WorkItem)));
-  CK(cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+  // per-step launches of the column strips alternate the order of the
+  // lattices from step to step (odd steps take each part of a class's list,
+  // tall and short segments, back to front): a step starts on the rows the
+  // previous one wrote last, which may still be in L2
+  const bool alt = cols_mode && !c->persistent;
+  std::vector<WorkItem> rev(items);
+  if (alt)
+    for (int j = 0; j < (int)c->cls.size(); ++j) {
+      const int b0 = c->cls_beg[j], n = c->cls_n[j];
+      const int nt = j < (int)c->cls_tall.size() ? c->cls_tall[j] : n;
+      std::reverse(rev.begin() + b0, rev.begin() + b0 + nt);
+      std::reverse(rev.begin() + b0 + nt, rev.begin() + b0 + n);
+    }
+  const size_t nb = items.size() * sizeof(WorkItem);
+  CK(cudaMalloc(&c->d_items, 2 * nb));
+  CK(cudaMemcpy(c->d_items, items.data(), nb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_items + items.size(), rev.data(), nb, cudaMemcpyHostToDevice));
+  c->alt_items = alt;
   c->n_items = (int)items.size();
   c->h_items = items;
   c->h_nbr_off.assign(items.size() + 1, 0);
@@ -925,8 +945,9 @@ extern "C" lbm_status lbm_init_droplet(lbm_ctx* c, int inst, double x0, double y
 // one time step: one launch per parameter class
 static cudaError_t launch_one_step(lbm_ctx* c, int parity, cudaStream_t s) {
   for (size_t j = 0; j < c->cls.size(); ++j) {
-    cudaError_t e = launch_step(c->prec, c->cls[j], c->d_desc, c->d_items + c->cls_beg[j],
-                                c->cls_n[j], parity, c->bx_used, c->stages_used, s);
+    const WorkItem* it = c->d_items + c->cls_beg[j] + (c->alt_items && (parity & 1) ? c->n_items : 0);
+    cudaError_t e = launch_step(c->prec, c->cls[j], c->d_desc, it, c->cls_n[j], parity, c->bx_used,
+                                c->stages_used, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
