@@ -161,6 +161,26 @@ def test_column_pair_strips_bitwise(cuda, launch):
         assert np.array_equal(got.populations(i), ref.populations(i)), (i, launch)
 
 
+@pytest.mark.parametrize("launch", [dict(), dict(persistent=True)])
+def test_column_pair_strips_narrow_and_exact_widths(cuda, launch):
+    """Widths at the edges of the column-pair geometry: 4 columns (every
+    16-byte piece of a row buffer wraps around the lattice many times, the
+    lanes past the lattice hold repeated columns), 8, and strips that end
+    exactly at 60 and 64 columns, bit for bit against the block rows."""
+    specs = []
+    for fsi, gw, nx, ny in [("modified", 0.1, 4, 9), ("density", -0.05, 8, 12),
+                            ("psi", 0.75, 60, 20), ("modified", -0.1, 64, 18),
+                            ("density", 0.07, 120, 23)]:
+        specs.append(dict(nx=nx, ny=ny, params=gpu_params(prec="fp32"),
+                          solid=inputs.flat_walls(nx, ny), fsi=fsi, gw=gw,
+                          drop=(nx / 2, 0.5, min(nx, ny) / 3, 2.0)))
+    ref = _run_batch(specs, 90, dict(stages=1))
+    got = _run_batch(specs, 90, launch)
+    assert got.launch()["pipeline"] == 4
+    for i in range(len(specs)):
+        assert np.array_equal(got.populations(i), ref.populations(i)), (i, launch)
+
+
 def test_column_pairs_need_widths_multiple_of_4(cuda):
     """A batch with a width that is not a multiple of 4 keeps the two-row
     strips, asked for or not."""
