@@ -510,19 +510,42 @@ static lbm_status build_items(lbm_ctx* c) {
   // persistent launch of those takes one row per lane)
   bool cols_ok = c->prec == LBM_FP32_SHIFTED;
   for (auto& I : c->inst) cols_ok = cols_ok && (I.nx % 4 == 0);
-  const bool cols_mode = cols_ok && (c->stages == 0 || c->stages == 4);
-  const bool warp_mode = cols_mode || c->stages == 0 || c->stages == 2 || c->stages == 3 ||
-                         c->stages == 4;
-  const bool two_rows = warp_mode && !cols_mode && c->stages != 3 &&
-                        c->prec == LBM_FP32_SHIFTED;
-  int bx = c->bx;
-  if (bx <= 0) {
-    // widest instance decides; whole rows up to 512 threads, else 256-wide strips
+  // the block width of block rows: the widest instance decides; whole rows
+  // up to 512 threads, else 256-wide strips
+  int bx_rows = 0;
+  {
     int maxnx = 0;
     for (auto& I : c->inst) maxnx = std::max(maxnx, I.nx);
-    if (maxnx + 2 <= 512) bx = ((maxnx + 2 + 31) / 32) * 32;
-    else bx = 256;
+    bx_rows = maxnx + 2 <= 512 ? ((maxnx + 2 + 31) / 32) * 32 : 256;
   }
+  // FP64 with the automatic pipeline: block rows where the batch gives at
+  // least 1.5 waves of them (one block per SM), warp strips otherwise.  A
+  // block row of up to 510 columns has 2 halo columns, a warp strip 2 of
+  // 32: block rows issue ~6% fewer FP64 operations, the bound of the FP64
+  // step (sweep 3.61k against 3.45k MLUPS, 8192x4096 4.04k against 3.94k),
+  // but a single small lattice leaves most SMs idle in them (256x128: 46
+  // against 765 MLUPS).
+  int stages = c->stages;
+  if (c->prec == LBM_FP64 && stages == 0 && !c->persistent) {
+    const int bxr = c->bx > 0 ? std::max(32, std::min(512, ((c->bx + 31) / 32) * 32)) : bx_rows;
+    const int colsr = bxr - 2;
+    long long nb = 0;
+    for (auto& I : c->inst) {
+      const int hmax_rows = 64;
+      const int hr = c->h > 0 ? c->h : (I.ny + (I.ny + hmax_rows - 1) / hmax_rows - 1) /
+                                           ((I.ny + hmax_rows - 1) / hmax_rows);
+      nb += (long long)((I.nx + colsr - 1) / colsr) * ((I.ny + hr - 1) / hr);
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (2 * nb >= 3LL * std::max(sms, 1)) stages = 1;
+  }
+  const bool cols_mode = cols_ok && (stages == 0 || stages == 4);
+  const bool warp_mode = cols_mode || stages == 0 || stages == 2 || stages == 3 || stages == 4;
+  const bool two_rows = warp_mode && !cols_mode && stages != 3 && c->prec == LBM_FP32_SHIFTED;
+  int bx = c->bx;
+  if (bx <= 0) bx = bx_rows;
   // warp strips: 8 warps per block; 4 for two rows per lane (128 registers
   // a thread: four blocks, 16 warps per SM)
   if (warp_mode && c->bx <= 0) bx = cols_mode ? 64 : (two_rows ? 128 : 256);
@@ -726,7 +749,7 @@ static lbm_status build_items(lbm_ctx* c) {
   // TMA pipeline: FP32 storage, every lattice width a multiple of 4
   bool tma_ok = c->prec != LBM_FP64;
   for (auto& I : c->inst) tma_ok = tma_ok && (I.nx % 4 == 0);
-  int S = c->stages == 0 ? 8 : c->stages;
+  int S = stages == 0 ? 8 : stages;
   // the ring must fit the per-block shared-memory limit; the pipeline needs
   // at least 8 stages (rows y-1..y+2 in use while later rows are in flight)
   int dev = 0, optin = 0;
@@ -734,8 +757,8 @@ static lbm_status build_items(lbm_ctx* c) {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   while (S >= 8 && tma_smem_bytes(bx, S) > (size_t)optin) S /= 2;
   c->stages_used = cols_mode   ? PIPE_COLS
-                   : warp_mode ? (c->stages == 3 ? PIPE_WARP1 : PIPE_WARP)
-                               : ((tma_ok && c->stages != 1 && S >= 8) ? S : 0);
+                   : warp_mode ? (stages == 3 ? PIPE_WARP1 : PIPE_WARP)
+                               : ((tma_ok && stages != 1 && S >= 8) ? S : 0);
   return LBM_OK;
 }
 

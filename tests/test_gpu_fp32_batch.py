@@ -181,6 +181,25 @@ def test_column_pair_strips_narrow_and_exact_widths(cuda, launch):
         assert np.array_equal(got.populations(i), ref.populations(i)), (i, launch)
 
 
+def test_fp64_automatic_pipeline(cuda):
+    """FP64 with the automatic pipeline: block rows for a batch of 1.5 waves
+    of them or more (the 72 lattices of 400x200: 288 block rows), warp strips
+    for a small one; the two give the same populations."""
+    specs = []
+    for k in range(72):
+        nx, ny = 400, 200
+        specs.append(dict(nx=nx, ny=ny, params=gpu_params(prec="fp64"),
+                          solid=inputs.flat_walls(nx, ny), fsi=("density", "psi", "modified")[k % 3],
+                          gw=0.05 * (k % 5 - 2), drop=(nx / 2, 0.5, 50.0, 4.0)))
+    big = _run_batch(specs, 20)
+    assert big.launch()["pipeline"] == 1
+    strips = _run_batch(specs, 20, dict(stages=3))
+    for i in (0, 35, 71):
+        assert np.array_equal(big.populations(i), strips.populations(i)), i
+    small = _run_batch(specs[:3], 2)
+    assert small.launch()["pipeline"] == 3
+
+
 def test_column_pairs_need_widths_multiple_of_4(cuda):
     """A batch with a width that is not a multiple of 4 keeps the two-row
     strips, asked for or not."""
