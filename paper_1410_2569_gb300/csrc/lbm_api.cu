@@ -607,6 +607,9 @@ static lbm_status build_items(lbm_ctx* c) {
       // many strips as possible but no more than one per resident warp
       while (hmax < maxny && count(hmax) > slots) hmax *= 2;
       while (hmax > 2 && count(hmax / 2) <= slots) hmax /= 2;
+      // then row by row: the lowest height that still fits (64 uneven
+      // lattices: 2383 strips instead of 1755 for 2432 warps, +9% MLUPS)
+      while (hmax > 2 && count(hmax - 1) <= slots) --hmax;
     } else if (cols_mode) {
       // the tallest segments that still give 3.5 waves of strips.  Fewer
       // waves leave SMs idle at the end of the step; shorter segments spend
