@@ -418,7 +418,10 @@ lbm_status lbm_strip_neighbours(int nx, int ny, int h, int* n_items, int* items3
    as items4[4 i .. 4 i + 3] = inst, x0, y0, y1.  With persistent warp strips
    (lbm_set_launch persistent = 1) nbr[off[i] .. off[i+1]) lists the items
    item i waits for between steps, by the rule of lbm_strip_neighbours;
-   otherwise every list is empty.  *n_items and *n_nbr receive the counts;
+   otherwise every list is empty.  The items are listed in the order the
+   even steps launch them (per parameter set; FP32 column-pair strips per
+   step: tall segments first, then short ones, and odd steps take each of
+   the two parts in reverse).  *n_items and *n_nbr receive the counts;
    with items4, off or nbr NULL only the counts are returned.  cap is the
    capacity of each of items4, off (n_items + 1) and nbr, in ints; LBM_ERR_ARG
    if one is too small or a count pointer is NULL. */
