@@ -470,7 +470,7 @@ def batched_uneven(stream, steps=1000):
     t = lat.autotune(steps=20)
     dt = time_device(lat, stream, steps, steps)
     out["autotuned"] = round(nodes * steps / dt / 1e6, 1)
-    out["autotuned_shape"] = {k: t[k] for k in ("bx", "h", "stages")}
+    out["autotuned_shape"] = {k: t[k] for k in ("bx", "h", "stages", "persistent")}
     lat.close()
     return out
 

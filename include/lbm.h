@@ -360,12 +360,15 @@ lbm_status lbm_load(lbm_ctx* ctx, const char* path);
 
 /* (An implementation call; the paper has no counterpart.)  Times lbm_step
    over `steps` steps for a fixed list of launch shapes
-   (pipeline, block width, rows per block) on the context's own lattices and
-   keeps the fastest.  The state and the step counter are restored after
-   every trial, so the call changes nothing but the launch shape; results do
-   not depend on the shape.  Outputs (any may be NULL): the chosen bx, h and
-   stages (as in lbm_set_launch; h = 0 is the automatic height) and its time
-   per step in ms. */
+   (pipeline, block width, rows per block, per-step or persistent launch)
+   on the context's own lattices and keeps the fastest; the persistent
+   shapes are tried only where the batch has one parameter set.  The state
+   and the step counter are restored after every trial, so the call changes
+   nothing but the launch shape (lbm_get_launch reports it, persistent flag
+   included); results do not depend on the shape.  The graph setting is
+   kept.  Outputs (any may be NULL): the chosen bx, h and stages (as in
+   lbm_set_launch; h = 0 is the automatic height) and its time per step in
+   ms. */
 lbm_status lbm_autotune(lbm_ctx* ctx, int steps, int* bx, int* h, int* stages, double* ms);
 
 /* Self-test of the bounded device-side wait used by the persistent step

@@ -1866,18 +1866,19 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, int steps, int* bx_out, int* h_ou
     }
   };
   struct Cand {
-    int bx, h, stages;
+    int bx, h, stages, persistent;
   };
   // FP32 warp strips with two columns per lane, warp strips (two rows per
   // lane with FP32 storage: even h), warp strips one row per lane, block
-  // rows, TMA block rows
-  std::vector<Cand> cands = {{128, 0, 4},  {128, 8, 4},  {128, 16, 4}, {128, 32, 4},
-                             {64, 0, 4},   {256, 0, 4},
-                             {128, 0, 2},  {128, 4, 2},  {128, 8, 2},  {128, 16, 2},
-                             {128, 24, 2}, {128, 32, 2}, {64, 32, 2},  {256, 32, 2},
-                             {256, 0, 3},  {256, 8, 3},  {256, 25, 3}, {256, 32, 3}, {128, 32, 3},
-                             {224, 32, 1}, {224, 50, 1}, {416, 50, 1}, {224, 50, 8},
-                             {416, 50, 8}};
+  // rows, TMA block rows, each launched per step; then the persistent warp
+  // strips (one parameter set only)
+  std::vector<Cand> cands = {
+      {128, 0, 4, 0},  {128, 8, 4, 0},  {128, 16, 4, 0}, {128, 32, 4, 0}, {64, 0, 4, 0},
+      {256, 0, 4, 0},  {128, 0, 2, 0},  {128, 4, 2, 0},  {128, 8, 2, 0},  {128, 16, 2, 0},
+      {128, 24, 2, 0}, {128, 32, 2, 0}, {64, 32, 2, 0},  {256, 32, 2, 0}, {256, 0, 3, 0},
+      {256, 8, 3, 0},  {256, 25, 3, 0}, {256, 32, 3, 0}, {128, 32, 3, 0}, {224, 32, 1, 0},
+      {224, 50, 1, 0}, {416, 50, 1, 0}, {224, 50, 8, 0}, {416, 50, 8, 0}, {64, 0, 4, 1},
+      {128, 0, 4, 1},  {256, 0, 3, 1}};
   const int saved[5] = {c->bx, c->h, c->persistent, c->use_graph, c->stages};
   c->persistent = 0;
   c->use_graph = 0;
@@ -1890,6 +1891,7 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, int steps, int* bx_out, int* h_ou
     c->bx = q.bx;
     c->h = q.h;
     c->stages = q.stages;
+    c->persistent = q.persistent;
     if (build_items(c) != LBM_OK) continue;
     if (q.stages >= 8 && c->stages_used < 8) continue;  // TMA not applicable here
     if (q.stages == 4 && c->stages_used != PIPE_COLS) continue;  // widths not multiples of 4
@@ -1912,7 +1914,7 @@ extern "C" lbm_status lbm_autotune(lbm_ctx* c, int steps, int* bx_out, int* h_ou
   c->bx = bestc.bx;
   c->h = bestc.h;
   c->stages = bestc.stages;
-  c->persistent = saved[2];
+  c->persistent = bestc.persistent;
   c->use_graph = saved[3];
   st = build_items(c);
   cleanup();

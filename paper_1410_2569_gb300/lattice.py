@@ -280,10 +280,12 @@ class Lattice:
         check(self._L.lbm_load(self._h, str(path).encode()))
 
     def autotune(self, steps=20):
-        """Pick the fastest launch shape for these lattices (lbm_autotune);
-        returns dict(bx, h, stages, ms_per_step)."""
+        """Pick the fastest launch shape for these lattices, per-step or
+        persistent (lbm_autotune); returns dict(bx, h, stages, persistent,
+        ms_per_step)."""
         bx, h, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         ms = ctypes.c_double()
         check(self._L.lbm_autotune(self._h, int(steps), ctypes.byref(bx), ctypes.byref(h),
                                    ctypes.byref(st), ctypes.byref(ms)))
-        return dict(bx=bx.value, h=h.value, stages=st.value, ms_per_step=ms.value)
+        return dict(bx=bx.value, h=h.value, stages=st.value,
+                    persistent=self.launch()["persistent"], ms_per_step=ms.value)

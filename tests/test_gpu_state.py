@@ -67,6 +67,7 @@ def test_autotune_changes_only_the_launch_shape(cuda):
     before = [a.populations(i) for i in range(len(specs))]
     best = a.autotune(steps=4)
     assert best["ms_per_step"] > 0 and best["stages"] in (1, 2, 3, 4, 8)
+    assert best["persistent"] == a.launch()["persistent"]
     assert a.t == 40
     for i in range(len(specs)):
         assert np.array_equal(a.populations(i), before[i])
